@@ -1,0 +1,168 @@
+/*
+ * adp.h -- C ABI of libadp.so, the GB300 (sm_103a) hot path of ADP-beta solved
+ * by the Method of Adaptive Inexact Descent (MAID), arXiv 2502.09758.
+ *
+ * Problem (Eq. 2.5 with the finite-dimensional instantiation of Sec. 3.2):
+ *
+ *   min_b  ell(b) = g(x^(b)) + r(b),   x^(b) = argmin_x h(x, b)
+ *   h(x, b) = 1/2 ||B x - y||^2 + alpha J(x)       (lower level, Eq. 2.5b)
+ *   g(x)    = ||A x - y||^2                          (upper fidelity)
+ *   r(b)    = beta (w0 ||b-a||^2 + ||D_h(b-a)||^2 + ||D_v(b-a)||^2)   (Sobolev, Sec. 4.2)
+ *
+ * B x is the discrete integral operator T(b, x) of Eq. 2.4: a centred periodic
+ * convolution per channel, (B x)[c,i,j] = sum_{p,q} b[c,p,q] x[c,i-p+r,j-q+r]
+ * with r = (K-1)/2 and indices taken modulo H and W.  A is the same operator
+ * with the fixed kernel a.  J is an anisotropic smoothed total variation,
+ * J(x) = sum phi((D_h x)) + phi((D_v x)) with periodic forward differences.
+ *
+ * Layouts: images are planar C x H x W, row-major, contiguous; kernels are
+ * C x K x K, row-major, contiguous.  Element type: float for ADP_F32, double
+ * for ADP_F64 (the `prec` of the problem); every `void*` data argument below
+ * has that type.  All data pointers are DEVICE pointers on the problem's
+ * device, owned by the caller; the library reads inputs and writes only the
+ * outputs named on each call, and never frees caller memory.
+ *
+ * Execution: every call is ordered on the stream given at creation, launches
+ * one cooperative kernel, and returns after that stream has finished the call
+ * (scalar outputs are valid on return).  Calls on one problem must not run
+ * concurrently.  No C++ exception crosses this boundary.  Every device-side
+ * wait is bounded by `wait_timeout_s`; a wait that gives up returns
+ * ADP_ETIMEOUT and leaves the CUDA context usable.
+ */
+#ifndef ADP_H
+#define ADP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ADP_OK = 0,
+    ADP_EINVAL = 1,      /* bad argument (null pointer, size, unsupported K)      */
+    ADP_ENOMEM = 2,      /* workspace allocation failed                            */
+    ADP_ECUDA = 3,       /* CUDA runtime error (message in adp_last_error)          */
+    ADP_ENONFINITE = 4,  /* a NaN/Inf appeared in a norm or a dot product           */
+    ADP_ENOCONV = 5,     /* an iterative solve hit its cap; outputs are valid       */
+    ADP_ELSFAIL = 6,     /* MAID backtracking rounds exhausted; b unchanged         */
+    ADP_ETIMEOUT = 7     /* a bounded device-side wait gave up                      */
+} adp_status;
+
+typedef enum { ADP_F64 = 0, ADP_F32 = 1 } adp_precision;
+
+typedef enum {
+    ADP_REG_HUBER_TV = 0,  /* phi(t) = t^2/(2 gamma) if |t| <= gamma else |t| - gamma/2  */
+    ADP_REG_SQRT_TV = 1,   /* phi(t) = sqrt(t^2 + nu^2) - nu  (Sec. 4.2, smoothed TV)   */
+    ADP_REG_QUAD = 2       /* phi(t) = t^2 / 2  (quadratic; closed-form checks)          */
+} adp_reg;
+
+typedef struct {
+    int C, H, W, K;          /* channels, image size, odd kernel size K (1..63)          */
+    double alpha;            /* lower-level weight of J                                   */
+    double reg_param;        /* gamma (Huber) or nu (sqrt); ignored for ADP_REG_QUAD      */
+    int reg;                 /* adp_reg                                                   */
+    double beta;             /* Sobolev weight of the upper level                         */
+    double sobolev_w0;       /* weight of ||b-a||^2 inside the H1 norm (1 full, 0 semi)  */
+    int prec;                /* adp_precision                                             */
+    double wait_timeout_s;   /* bound on each device-side wait; <= 0 selects 2 s          */
+} adp_params;
+
+typedef struct adp_problem adp_problem;
+
+/* Creates a problem for data y (C x H x W) and the fixed kernel a of A
+ * (C x K x K); both are copied into library-owned device memory, so the caller
+ * may free them afterwards.  `stream` is a cudaStream_t (NULL = legacy default
+ * stream).  Allocates the workspace (about 12 images) with cudaMalloc. */
+adp_status adp_problem_create(const adp_params *params, const void *y, const void *a,
+                              void *stream, adp_problem **out);
+void adp_problem_destroy(adp_problem *p);
+
+/* out = B x (Eq. 2.4, convolution with b).  x, out: C x H x W; b: C x K x K. */
+adp_status adp_apply_B(adp_problem *p, const void *b, const void *x, void *out);
+/* out = B^T z (the adjoint: correlation with b). */
+adp_status adp_apply_Bt(adp_problem *p, const void *b, const void *z, void *out);
+
+/* out = grad_x h(x, b) = B^T(B x - y) + alpha grad J(x)   (Prop. 1, gradient);
+ * *norm = ||out||_2 accumulated in FP64.  `out` may be NULL. */
+adp_status adp_grad_lower(adp_problem *p, const void *b, const void *x, void *out, double *norm);
+
+/* out = grad^2_x h(x, b) v = B^T B v + alpha D^T(phi''(D x) . D v)   (Prop. 1, Hessian). */
+adp_status adp_hess_vec(adp_problem *p, const void *b, const void *x, const void *v, void *out);
+
+/* Algorithm 1, step 1: FISTA on h(., b) from the warm start held in x,
+ * stopped when ||grad_x h(y_k, b)|| <= eps (the test of Algorithm 1 with
+ * mu := 1) or after max_iters updates; x receives y_k.  Step 1/L_c per channel
+ * with L_c = ||b_c||_1^2 + 8 alpha sup phi''.  *iters = updates made,
+ * *gradnorm = ||grad_x h|| at the returned point.  Returns ADP_ENOCONV when
+ * the cap was reached (x still valid). */
+adp_status adp_lower_solve(adp_problem *p, const void *b, void *x, double eps, int max_iters,
+                           int *iters, double *gradnorm);
+
+/* Upper-level loss ell = g(x) + r(b) and ||grad_x ell|| = ||grad g(x)||, the
+ * terms of Eq. 3.4.  gradx (optional, may be NULL) receives grad g(x) =
+ * 2 A^T (A x - y). */
+adp_status adp_upper_loss(adp_problem *p, const void *b, const void *x, double *loss,
+                          double *gradx_norm, void *gradx);
+
+/* Algorithm 1, steps 2-3: conjugate gradients on grad^2_x h(x, b) q = rhs
+ * from the start held in q (pass zeros for the paper's q_0 = 0), stopped at
+ * ||residual|| <= delta or after max_iters iterations; then
+ * z = -(grad^2_{xb} h(x, b))^T q + grad r(b).  With rhs == NULL the right-hand
+ * side is grad g(x) (the hypergradient of Eq. 3.2); with an explicit rhs
+ * (C x H x W, e.g. an upstream gradient) the grad r(b) term is left out.
+ * q: C x H x W in/out; z: C x K x K out.  Returns ADP_ENOCONV at the cap. */
+adp_status adp_hypergrad(adp_problem *p, const void *b, const void *x, const void *rhs,
+                         double delta, int max_iters, void *q, void *z, int *cg_iters,
+                         double *resnorm);
+
+/* The kernel-gradient correlation of Algorithm 1, step 3, alone:
+ * out[c,p,q] = sum_{i,j} x[c,i-p+r,j-q+r] (B v)[c,i,j] + v[c,i-p+r,j-q+r] (B x - y)[c,i,j]
+ * = (grad^2_{xb} h(x, b))^T v.  out: C x K x K. */
+adp_status adp_cross_t(adp_problem *p, const void *b, const void *x, const void *v, void *out);
+
+/* State of Algorithm 2 carried between upper iterations, plus the report of
+ * the last call.  Initialise with adp_maid_init (paper defaults, Sec. 4.1). */
+typedef struct {
+    double eps, delta, step;          /* eps_k, delta_k, alpha_k                         */
+    double lambda;                    /* lambda of Eq. 3.4 (1e-4)                         */
+    double rho_up, rho_down;          /* 1.1, 0.5                                         */
+    double nu_up, nu_down;            /* 1.25, 0.5                                        */
+    double L_gx;                      /* Lipschitz constant of grad g; set by adp_maid_init */
+    int max_bt, max_rounds;           /* first inner-loop length (5), outer rounds (20)    */
+    int ll_max_iters, cg_max_iters;   /* 300 (Sec. 4.1), 1000                             */
+    int k;                            /* accepted upper iterations so far                  */
+    /* report of the last adp_maid_step */
+    int accepted, rounds, trials, ll_iters, cg_iters, ll_capped, cg_capped;
+    double loss, gradx_norm, znorm, psi;
+} adp_maid_state;
+
+/* Fills `s` with the paper's defaults and L_gx = 2 max_c ||a_c||_1^2. */
+adp_status adp_maid_init(adp_problem *p, adp_maid_state *s);
+
+/* One upper iteration of Algorithm 2 (MAID), entirely on the device in one
+ * cooperative launch: InexactGradient(b_k, eps_k, delta_k), then backtracking
+ * on psi <= 0 (Eq. 3.4) with lower-level re-solves warm-started from x~(b_k);
+ * on success b_{k+1} = b_k - alpha_k z_k and eps, delta, alpha grow; after a
+ * failed round eps and delta shrink and the gradient is recomputed.
+ * b (C x K x K) and x (C x H x W, x~(b_k) in, x~(b_{k+1}) out) are in/out; q
+ * (C x H x W) receives the last CG solution.  Returns ADP_ELSFAIL when all
+ * rounds failed (b, x unchanged; s reports the shrunk eps, delta, step). */
+adp_status adp_maid_step(adp_problem *p, adp_maid_state *s, void *b, void *x, void *q);
+
+/* Diagnostics of the last call on p: number of full-image convolution passes
+ * it executed (each is 2 K^2 C H W flops; the kernel-gradient correlation
+ * counts as two), and the number of CTAs of its cooperative launch. */
+long long adp_conv_passes_last(adp_problem *p);
+int adp_grid_size(adp_problem *p);
+/* Device time in ms of the last call's cooperative kernel, measured with CUDA
+ * events recorded on the problem's stream around the launch. */
+double adp_last_kernel_ms(adp_problem *p);
+
+/* Thread-local message for the last failing call on this thread. */
+const char *adp_last_error(void);
+const char *adp_status_string(adp_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADP_H */

@@ -1,0 +1,385 @@
+// libadp: GB300 (sm_103a) hot path of ADP-beta solved by MAID (arXiv 2502.09758).
+//
+// One cooperative, persistent kernel per C-ABI call.  A call runs a program of
+// phases (convolution passes over image tiles, element-wise updates, FP64
+// reductions) separated by a bounded grid barrier; the iteration control of
+// FISTA (Algorithm 1, step 1), CG (Algorithm 1, step 2) and MAID (Algorithm 2)
+// runs on the device, identically in every CTA, from reduction results that
+// every CTA sums in the same order.  The host sees only the final scalars.
+//
+// This file is the host side: argument checks, workspace, cooperative launches.
+// The kernels live in adp_engine.cuh, instantiated in adp_f32.cu / adp_f64.cu.
+#include "adp_device.cuh"
+#include "adp.h"
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <type_traits>
+
+// ====================================================================== host
+
+using namespace adp;
+
+namespace adp {
+const void *kernel_f32();
+const void *kernel_f64();
+} // namespace adp
+
+static thread_local char g_err[512];
+
+static adp_status set_err(adp_status s, const char *fmt, const char *a = "", long long v = 0)
+{
+    snprintf(g_err, sizeof g_err, fmt, a, v);
+    return s;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) return set_err(ADP_ECUDA, "%s (code %lld)", cudaGetErrorString(e_), (long long)e_); \
+    } while (0)
+
+struct adp_problem {
+    adp_params prm;
+    cudaStream_t stream;
+    int device, grid;
+    size_t smem;
+    size_t esize;
+    void *y, *a;
+    void *img[10];     // X0 X1 X2 U V G R P HP XT
+    void *BT, *ZK;
+    double *part, *zpart;
+    unsigned *bar;
+    DevOut *dout, *hout;
+    double *a_host;    // a in FP64 on the host (for L of grad g)
+    int TH, tiles_x, tiles_y, ntiles;
+    cudaEvent_t ev0, ev1;  // bracket the cooperative launch on the problem's stream
+    float last_ms;
+};
+
+template <typename T>
+static Ctx<T> make_ctx(const adp_problem *p)
+{
+    Ctx<T> c;
+    const adp_params &q = p->prm;
+    c.C = q.C; c.H = q.H; c.W = q.W; c.K = q.K; c.r = (q.K - 1) / 2; c.h = c.r > 1 ? c.r : 1;
+    c.TH = p->TH; c.tiles_x = p->tiles_x; c.tiles_y = p->tiles_y; c.ntiles = p->ntiles;
+    c.HW = (long long)q.H * q.W; c.N = c.HW * q.C;
+    c.reg = q.reg; c.alpha = q.alpha; c.rp = q.reg_param; c.beta = q.beta; c.w0 = q.sobolev_w0;
+    c.ddphi_max = q.reg == ADP_REG_QUAD ? 1.0 : 1.0 / q.reg_param;
+    c.y = (const T *)p->y; c.a = (const T *)p->a;
+    T **im[10] = {&c.X0, &c.X1, &c.X2, &c.U, &c.V, &c.G, &c.R, &c.P, &c.HP, &c.XT};
+    for (int i = 0; i < 10; ++i) *im[i] = (T *)p->img[i];
+    c.BT = (T *)p->BT; c.ZK = (T *)p->ZK;
+    c.part = p->part; c.zpart = p->zpart; c.bar = p->bar; c.out = p->dout;
+    double to = q.wait_timeout_s > 0 ? q.wait_timeout_s : 2.0;
+    c.timeout_ns = (long long)(to * 1e9);
+    return c;
+}
+
+template <typename T>
+static size_t smem_bytes(int TH, int K)
+{
+    const int r = (K - 1) / 2, h = r > 1 ? r : 1;
+    const size_t halo = (size_t)(TH + 2 * h) * (32 + 2 * h);
+    const size_t elems = 2 * halo + (size_t)(TH + 2) * 34 + 2 * (size_t)TH * 32 + (size_t)K * K;
+    return elems * sizeof(T);
+}
+
+template <typename T>
+static adp_status launch(adp_problem *p, Job<T> &jb)
+{
+    Ctx<T> cx = make_ctx<T>(p);
+    CK(cudaSetDevice(p->device));
+    CK(cudaMemsetAsync(p->bar, 0, 2 * sizeof(unsigned), p->stream));
+    CK(cudaMemsetAsync(p->dout, 0, sizeof(DevOut), p->stream));
+    void *args[] = {(void *)&cx, (void *)&jb};
+    const void *fn = std::is_same<T, float>::value ? kernel_f32() : kernel_f64();
+    CK(cudaEventRecord(p->ev0, p->stream));
+    CK(cudaLaunchCooperativeKernel(fn, dim3(p->grid), dim3(NT), args, p->smem, p->stream));
+    CK(cudaEventRecord(p->ev1, p->stream));
+    CK(cudaMemcpyAsync(p->hout, p->dout, sizeof(DevOut), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    CK(cudaEventElapsedTime(&p->last_ms, p->ev0, p->ev1));
+    const int st = p->hout->status;
+    if (st == ST_TIMEOUT) return set_err(ADP_ETIMEOUT, "device-side wait gave up after %s%lld ns", "", cx.timeout_ns);
+    if (st == ST_NONFINITE) return set_err(ADP_ENONFINITE, "non-finite value in a reduction%s", "", 0);
+    if (st != ST_OK) return set_err(ADP_ECUDA, "unexpected device status%s %lld", "", st);
+    return ADP_OK;
+}
+
+template <typename T>
+static adp_status run(adp_problem *p, Job<T> jb)
+{
+    return launch<T>(p, jb);
+}
+
+static adp_status dispatch_job(adp_problem *p, int mode, const void *b, const void *x, void *xo, const void *v,
+                               void *q, void *z, void *bio, double eps, double delta, int max_iters,
+                               const MaidIn *mi)
+{
+    if (p->prm.prec == ADP_F32) {
+        Job<float> j{};
+        j.mode = mode; j.b = (const float *)b; j.x = (const float *)x; j.xo = (float *)xo;
+        j.v = (const float *)v; j.q = (float *)q; j.z = (float *)z; j.bio = (float *)bio;
+        j.eps = eps; j.delta = delta; j.max_iters = max_iters;
+        if (mi) j.maid = *mi;
+        return run<float>(p, j);
+    }
+    Job<double> j{};
+    j.mode = mode; j.b = (const double *)b; j.x = (const double *)x; j.xo = (double *)xo;
+    j.v = (const double *)v; j.q = (double *)q; j.z = (double *)z; j.bio = (double *)bio;
+    j.eps = eps; j.delta = delta; j.max_iters = max_iters;
+    if (mi) j.maid = *mi;
+    return run<double>(p, j);
+}
+
+extern "C" {
+
+const char *adp_last_error(void) { return g_err; }
+
+const char *adp_status_string(adp_status s)
+{
+    switch (s) {
+    case ADP_OK: return "ok";
+    case ADP_EINVAL: return "invalid argument";
+    case ADP_ENOMEM: return "out of device memory";
+    case ADP_ECUDA: return "CUDA error";
+    case ADP_ENONFINITE: return "non-finite value";
+    case ADP_ENOCONV: return "iteration cap reached";
+    case ADP_ELSFAIL: return "line search failed";
+    case ADP_ETIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+void adp_problem_destroy(adp_problem *p)
+{
+    if (!p) return;
+    cudaSetDevice(p->device);
+    cudaStreamSynchronize(p->stream);
+    void *ptrs[] = {p->y, p->a, p->BT, p->ZK, p->part, p->zpart, p->bar, p->dout};
+    for (void *q : ptrs) if (q) cudaFree(q);
+    for (void *q : p->img) if (q) cudaFree(q);
+    if (p->hout) cudaFreeHost(p->hout);
+    if (p->ev0) cudaEventDestroy(p->ev0);
+    if (p->ev1) cudaEventDestroy(p->ev1);
+    free(p->a_host);
+    free(p);
+}
+
+adp_status adp_problem_create(const adp_params *prm, const void *y, const void *a, void *stream,
+                              adp_problem **out)
+{
+    if (!prm || !y || !a || !out) return set_err(ADP_EINVAL, "null argument%s", "", 0);
+    *out = nullptr;
+    const adp_params &q = *prm;
+    if (q.C < 1 || q.C > MAXC) return set_err(ADP_EINVAL, "C must be in [1, 64]%s (got %lld)", "", q.C);
+    if (q.H < 1 || q.W < 1) return set_err(ADP_EINVAL, "H and W must be positive%s", "", 0);
+    if (q.K < 1 || q.K > KMAX || (q.K % 2) == 0)
+        return set_err(ADP_EINVAL, "K must be odd and in [1, 63]%s (got %lld)", "", q.K);
+    if (q.prec != ADP_F32 && q.prec != ADP_F64) return set_err(ADP_EINVAL, "unsupported precision%s", "", 0);
+    if (q.reg < 0 || q.reg > 2) return set_err(ADP_EINVAL, "unknown regulariser%s", "", 0);
+    if (q.reg != ADP_REG_QUAD && !(q.reg_param > 0)) return set_err(ADP_EINVAL, "reg_param must be > 0%s", "", 0);
+    if (!(q.alpha >= 0) || !(q.beta >= 0)) return set_err(ADP_EINVAL, "alpha and beta must be >= 0%s", "", 0);
+
+    adp_problem *p = (adp_problem *)calloc(1, sizeof(adp_problem));
+    if (!p) return set_err(ADP_ENOMEM, "host allocation failed%s", "", 0);
+    p->prm = q;
+    p->stream = (cudaStream_t)stream;
+    p->esize = q.prec == ADP_F32 ? sizeof(float) : sizeof(double);
+    p->TH = (q.prec == ADP_F32 ? Cfg<float>::MR : Cfg<double>::MR) * NW;
+    p->tiles_x = (q.W + 31) / 32;
+    p->tiles_y = (q.H + p->TH - 1) / p->TH;
+    p->ntiles = q.C * p->tiles_x * p->tiles_y;
+    p->smem = q.prec == ADP_F32 ? smem_bytes<float>(p->TH, q.K) : smem_bytes<double>(p->TH, q.K);
+
+    adp_status st = ADP_OK;
+#define CKC(call)                                                                            \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            st = set_err(e_ == cudaErrorMemoryAllocation ? ADP_ENOMEM : ADP_ECUDA, "%s (code %lld)", \
+                         cudaGetErrorString(e_), (long long)e_);                             \
+            adp_problem_destroy(p);                                                          \
+            return st;                                                                       \
+        }                                                                                    \
+    } while (0)
+
+    CKC(cudaGetDevice(&p->device));
+    int nsm = 0, maxsmem = 0;
+    CKC(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
+    CKC(cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    // static shared memory of the kernel is small (< 1 KB); keep a margin
+    if (p->smem + 1024 > (size_t)maxsmem) {
+        adp_problem_destroy(p);
+        return set_err(ADP_EINVAL, "kernel too large for shared memory%s (%lld bytes)", "", (long long)p->smem);
+    }
+    const void *kfn = q.prec == ADP_F32 ? kernel_f32() : kernel_f64();
+    CKC(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem));
+    int occ = 0;
+    CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, NT, p->smem));
+    if (occ < 1) {
+        adp_problem_destroy(p);
+        return set_err(ADP_EINVAL, "kernel cannot be resident%s", "", 0);
+    }
+    long long maxgrid = (long long)occ * nsm;
+    p->grid = (int)(p->ntiles < maxgrid ? p->ntiles : maxgrid);
+
+    const size_t N = (size_t)q.C * q.H * q.W, KK = (size_t)q.C * q.K * q.K;
+    CKC(cudaMalloc(&p->y, N * p->esize));
+    CKC(cudaMalloc(&p->a, KK * p->esize));
+    for (int i = 0; i < 10; ++i) CKC(cudaMalloc(&p->img[i], N * p->esize));
+    CKC(cudaMalloc(&p->BT, KK * p->esize));
+    CKC(cudaMalloc(&p->ZK, KK * p->esize));
+    CKC(cudaMalloc((void **)&p->part, (size_t)NSLOT * p->grid * sizeof(double)));
+    CKC(cudaMalloc((void **)&p->zpart, (size_t)p->grid * KK * sizeof(double)));
+    CKC(cudaMalloc((void **)&p->bar, 2 * sizeof(unsigned)));
+    CKC(cudaMalloc((void **)&p->dout, sizeof(DevOut)));
+    CKC(cudaMallocHost((void **)&p->hout, sizeof(DevOut)));
+    CKC(cudaEventCreate(&p->ev0));
+    CKC(cudaEventCreate(&p->ev1));
+    CKC(cudaMemcpyAsync(p->y, y, N * p->esize, cudaMemcpyDeviceToDevice, p->stream));
+    CKC(cudaMemcpyAsync(p->a, a, KK * p->esize, cudaMemcpyDeviceToDevice, p->stream));
+    for (int i = 0; i < 10; ++i) CKC(cudaMemsetAsync(p->img[i], 0, N * p->esize, p->stream));
+    p->a_host = (double *)malloc(KK * sizeof(double));
+    if (!p->a_host) { adp_problem_destroy(p); return set_err(ADP_ENOMEM, "host allocation failed%s", "", 0); }
+    if (q.prec == ADP_F32) {
+        float *tmp = (float *)malloc(KK * sizeof(float));
+        if (!tmp) { adp_problem_destroy(p); return set_err(ADP_ENOMEM, "host allocation failed%s", "", 0); }
+        CKC(cudaMemcpyAsync(tmp, a, KK * sizeof(float), cudaMemcpyDeviceToHost, p->stream));
+        CKC(cudaStreamSynchronize(p->stream));
+        for (size_t i = 0; i < KK; ++i) p->a_host[i] = tmp[i];
+        free(tmp);
+    } else {
+        CKC(cudaMemcpyAsync(p->a_host, a, KK * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+        CKC(cudaStreamSynchronize(p->stream));
+    }
+#undef CKC
+    *out = p;
+    return ADP_OK;
+}
+
+#define NEED(p, ...)                                                                  \
+    do {                                                                              \
+        if (!(p)) return set_err(ADP_EINVAL, "null problem%s", "", 0);                \
+        const void *ptrs_[] = {__VA_ARGS__};                                          \
+        for (const void *q_ : ptrs_)                                                  \
+            if (!q_) return set_err(ADP_EINVAL, "null data pointer%s", "", 0);        \
+    } while (0)
+
+adp_status adp_apply_B(adp_problem *p, const void *b, const void *x, void *out)
+{
+    NEED(p, b, x, out);
+    return dispatch_job(p, M_APPLY_B, b, x, out, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, nullptr);
+}
+
+adp_status adp_apply_Bt(adp_problem *p, const void *b, const void *z, void *out)
+{
+    NEED(p, b, z, out);
+    return dispatch_job(p, M_APPLY_BT, b, z, out, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, nullptr);
+}
+
+adp_status adp_grad_lower(adp_problem *p, const void *b, const void *x, void *out, double *norm)
+{
+    NEED(p, b, x);
+    adp_status s = dispatch_job(p, M_GRAD_LOWER, b, x, out, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, nullptr);
+    if (s == ADP_OK && norm) *norm = p->hout->gradnorm;
+    return s;
+}
+
+adp_status adp_hess_vec(adp_problem *p, const void *b, const void *x, const void *v, void *out)
+{
+    NEED(p, b, x, v, out);
+    return dispatch_job(p, M_HESS_VEC, b, x, out, v, nullptr, nullptr, nullptr, 0, 0, 0, nullptr);
+}
+
+adp_status adp_lower_solve(adp_problem *p, const void *b, void *x, double eps, int max_iters, int *iters,
+                           double *gradnorm)
+{
+    NEED(p, b, x);
+    if (max_iters < 0) return set_err(ADP_EINVAL, "max_iters must be >= 0%s", "", 0);
+    adp_status s = dispatch_job(p, M_LOWER_SOLVE, b, x, x, nullptr, nullptr, nullptr, nullptr, eps, 0, max_iters,
+                                nullptr);
+    if (s != ADP_OK) return s;
+    if (iters) *iters = p->hout->iters;
+    if (gradnorm) *gradnorm = p->hout->gradnorm;
+    return p->hout->capped ? ADP_ENOCONV : ADP_OK;
+}
+
+adp_status adp_upper_loss(adp_problem *p, const void *b, const void *x, double *loss, double *gradx_norm,
+                          void *gradx)
+{
+    NEED(p, b, x);
+    adp_status s = dispatch_job(p, M_UPPER_LOSS, b, x, gradx, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, nullptr);
+    if (s != ADP_OK) return s;
+    if (loss) *loss = p->hout->loss;
+    if (gradx_norm) *gradx_norm = p->hout->gradx_norm;
+    return ADP_OK;
+}
+
+adp_status adp_hypergrad(adp_problem *p, const void *b, const void *x, const void *rhs, double delta,
+                         int max_iters, void *q, void *z, int *cg_iters, double *resnorm)
+{
+    NEED(p, b, x, q, z);
+    if (max_iters < 0) return set_err(ADP_EINVAL, "max_iters must be >= 0%s", "", 0);
+    adp_status s = dispatch_job(p, M_HYPERGRAD, b, x, nullptr, rhs, q, z, nullptr, 0, delta, max_iters, nullptr);
+    if (s != ADP_OK) return s;
+    if (cg_iters) *cg_iters = p->hout->cg_iters;
+    if (resnorm) *resnorm = p->hout->resnorm;
+    return p->hout->capped ? ADP_ENOCONV : ADP_OK;
+}
+
+adp_status adp_cross_t(adp_problem *p, const void *b, const void *x, const void *v, void *out)
+{
+    NEED(p, b, x, v, out);
+    return dispatch_job(p, M_CROSS, b, x, nullptr, v, nullptr, out, nullptr, 0, 0, 0, nullptr);
+}
+
+adp_status adp_maid_init(adp_problem *p, adp_maid_state *s)
+{
+    if (!p || !s) return set_err(ADP_EINVAL, "null argument%s", "", 0);
+    memset(s, 0, sizeof *s);
+    s->eps = 1e-2; s->delta = 1e-2; s->step = 0.1;
+    s->lambda = 1e-4; s->rho_up = 1.1; s->rho_down = 0.5; s->nu_up = 1.25; s->nu_down = 0.5;
+    s->max_bt = 5; s->max_rounds = 20; s->ll_max_iters = 300; s->cg_max_iters = 1000;
+    const int K = p->prm.K;
+    double m = 0.0;
+    for (int c = 0; c < p->prm.C; ++c) {
+        double l1 = 0.0;
+        for (int e = 0; e < K * K; ++e) l1 += fabs(p->a_host[(size_t)c * K * K + e]);
+        if (l1 * l1 > m) m = l1 * l1;
+    }
+    s->L_gx = 2.0 * m;
+    return ADP_OK;
+}
+
+adp_status adp_maid_step(adp_problem *p, adp_maid_state *s, void *b, void *x, void *q)
+{
+    NEED(p, s, b, x, q);
+    if (s->max_bt < 1 || s->max_rounds < 1 || s->ll_max_iters < 0 || s->cg_max_iters < 0)
+        return set_err(ADP_EINVAL, "invalid MAID state%s", "", 0);
+    MaidIn mi;
+    mi.eps = s->eps; mi.delta = s->delta; mi.step = s->step; mi.lambda = s->lambda;
+    mi.rho_up = s->rho_up; mi.rho_down = s->rho_down; mi.nu_up = s->nu_up; mi.nu_down = s->nu_down;
+    mi.L_gx = s->L_gx; mi.max_bt = s->max_bt; mi.max_rounds = s->max_rounds;
+    mi.ll_max_iters = s->ll_max_iters; mi.cg_max_iters = s->cg_max_iters; mi.k = s->k;
+    adp_status st = dispatch_job(p, M_MAID, nullptr, x, nullptr, nullptr, q, nullptr, b, 0, 0, 0, &mi);
+    if (st != ADP_OK) return st;
+    const DevOut *o = p->hout;
+    s->eps = o->eps; s->delta = o->delta; s->step = o->step; s->k = o->k;
+    s->accepted = o->accepted; s->rounds = o->rounds; s->trials = o->trials;
+    s->ll_iters = o->ll_iters; s->cg_iters = o->cg_iters; s->ll_capped = o->ll_capped; s->cg_capped = o->cg_capped;
+    s->loss = o->loss; s->gradx_norm = o->gradx_norm; s->znorm = o->znorm; s->psi = o->psi;
+    return o->accepted ? ADP_OK : ADP_ELSFAIL;
+}
+
+long long adp_conv_passes_last(adp_problem *p) { return p ? p->hout->conv_passes : -1; }
+int adp_grid_size(adp_problem *p) { return p ? p->grid : -1; }
+double adp_last_kernel_ms(adp_problem *p) { return p ? (double)p->last_ms : -1.0; }
+
+} // extern "C"
