@@ -31,6 +31,11 @@ METRIC = "MAID time-to-tolerance (s) vs plain FP32 GPU; Mpixel·iter/s of fused 
 UNIT = "Mvalue·iter/s (values = C·H·W; iters = FISTA + CG iterations)"
 WORKLOAD = "rgb256_k15_motion"
 SM_COUNT, FP32_LANES = 152, 128
+# MAID start for this workload (eps_0 = delta_0, alpha_0): the paper's 1e-2 / 0.1
+# are sized for its own scaling; these were picked by a grid search over
+# eps_0 in {1e-2, 1e-3, 1e-4} x alpha_0 in {1e-1, 1e-5, 1e-6, 1e-7} (every
+# step accepted, least time), as the paper picks alpha and beta by grid search
+EPS0, STEP0 = 1e-4, 1e-6
 
 
 def peaks():
@@ -160,7 +165,7 @@ def run_ours(args):
     prob = adp.Problem(adp.Params(C, H, W, K, alpha=1e-2, reg_param=1e-2, beta=0.3), y, a)
     b, x = a.clone(), y.clone()
     q = torch.zeros_like(x)
-    st = prob.maid_init()
+    st = prob.maid_init(eps=EPS0, delta=EPS0, step=STEP0)
     for _ in range(args.warmup):
         prob.maid_step(st, b, x, q)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
@@ -231,7 +236,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": tot_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "C": C, "H": H, "W": W, "K": K, "alpha": 1e-2, "huber": 1e-2,
-                   "beta": 0.3, "l2": "flushed between timed steps (256 MB write)",
+                   "beta": 0.3, "maid_eps0": EPS0, "maid_step0": STEP0,
+                   "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "maid": {"upper_iters_timed": args.steps, "accepted": accepted,
                  "fused_iters_per_step": iters / args.steps, "eps_end": st.eps,

@@ -153,9 +153,21 @@ adp_status adp_maid_step(adp_problem *p, adp_maid_state *s, void *b, void *x, vo
  * counts as two), and the number of CTAs of its cooperative launch. */
 long long adp_conv_passes_last(adp_problem *p);
 int adp_grid_size(adp_problem *p);
+/* Warps per CTA of the problem's launches (chosen from the shared memory a
+ * warp's halo tiles need for this kernel size). */
+int adp_warps_per_cta(adp_problem *p);
 /* Device time in ms of the last call's cooperative kernel, measured with CUDA
  * events recorded on the problem's stream around the launch. */
 double adp_last_kernel_ms(adp_problem *p);
+
+/* Tracing (diagnostics).  With cap > 0, later calls on p record, for the first
+ * cap grid barriers of each launch, the device global timer (ns) when CTA 0
+ * arrived at and left the barrier; cap = 0 turns tracing off.  Allocates (and
+ * frees) a device buffer of 2 * cap values with cudaMalloc/cudaFree.
+ * adp_trace_read copies the (arrive, leave) pairs of the last call to host
+ * memory (at most cap pairs) and returns how many pairs it wrote, or -1. */
+adp_status adp_trace_enable(adp_problem *p, int cap);
+int adp_trace_read(adp_problem *p, long long *host_out, int cap);
 
 /* Thread-local message for the last failing call on this thread. */
 const char *adp_last_error(void);

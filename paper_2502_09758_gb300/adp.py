@@ -28,7 +28,8 @@ ADP_REG_HUBER_TV, ADP_REG_SQRT_TV, ADP_REG_QUAD = 0, 1, 2
 EXPORTS = ("adp_problem_create", "adp_problem_destroy", "adp_apply_B", "adp_apply_Bt",
            "adp_grad_lower", "adp_hess_vec", "adp_lower_solve", "adp_upper_loss", "adp_hypergrad",
            "adp_cross_t", "adp_maid_init", "adp_maid_step", "adp_conv_passes_last",
-           "adp_grid_size", "adp_last_kernel_ms", "adp_last_error", "adp_status_string")
+           "adp_grid_size", "adp_warps_per_cta", "adp_last_kernel_ms", "adp_trace_enable",
+           "adp_trace_read", "adp_last_error", "adp_status_string")
 
 
 class AdpError(RuntimeError):
@@ -85,7 +86,10 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
             "adp_maid_step": (i, [P, ct.POINTER(adp_maid_state), vp, vp, vp]),
             "adp_conv_passes_last": (ct.c_longlong, [P]),
             "adp_grid_size": (i, [P]),
+            "adp_warps_per_cta": (i, [P]),
             "adp_last_kernel_ms": (ct.c_double, [P]),
+            "adp_trace_enable": (i, [P, i]),
+            "adp_trace_read": (i, [P, ct.POINTER(ct.c_longlong), i]),
             "adp_last_error": (ct.c_char_p, []),
             "adp_status_string": (ct.c_char_p, [i]),
         }
@@ -267,8 +271,23 @@ class Problem:
     def grid_size(self) -> int:
         return int(self.lib.adp_grid_size(self.handle))
 
+    def warps_per_cta(self) -> int:
+        return int(self.lib.adp_warps_per_cta(self.handle))
+
     def last_kernel_ms(self) -> float:
         return float(self.lib.adp_last_kernel_ms(self.handle))
+
+    def trace_enable(self, cap: int):
+        _check(self.lib.adp_trace_enable(self.handle, int(cap)))
+        self._trace_cap = int(cap)
+
+    def trace_read(self):
+        """(arrive, leave) global-timer pairs (ns) of CTA 0 for the last call."""
+        import numpy as np
+        cap = getattr(self, "_trace_cap", 0)
+        buf = (ct.c_longlong * (2 * max(cap, 1)))()
+        n = self.lib.adp_trace_read(self.handle, buf, cap)
+        return np.array(buf[: 2 * max(n, 0)], dtype=np.int64).reshape(-1, 2)
 
 
 def adp_lower_solve(prob: Problem, b, x, eps, max_iters=300):

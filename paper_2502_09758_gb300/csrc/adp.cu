@@ -1,7 +1,7 @@
 // libadp: GB300 (sm_103a) hot path of ADP-beta solved by MAID (arXiv 2502.09758).
 //
 // One cooperative, persistent kernel per C-ABI call.  A call runs a program of
-// phases (convolution passes over image tiles, element-wise updates, FP64
+// phases (convolution passes over image strips, element-wise updates, FP64
 // reductions) separated by a bounded grid barrier; the iteration control of
 // FISTA (Algorithm 1, step 1), CG (Algorithm 1, step 2) and MAID (Algorithm 2)
 // runs on the device, identically in every CTA, from reduction results that
@@ -19,8 +19,6 @@
 #include <string.h>
 
 #include <type_traits>
-
-// ====================================================================== host
 
 using namespace adp;
 
@@ -46,17 +44,19 @@ static adp_status set_err(adp_status s, const char *fmt, const char *a = "", lon
 struct adp_problem {
     adp_params prm;
     cudaStream_t stream;
-    int device, grid;
-    size_t smem;
+    int device, grid, nw;  // CTAs of the cooperative launch, warps per CTA
+    size_t smem;           // dynamic shared memory per CTA (bytes)
     size_t esize;
     void *y, *a;
-    void *img[10];     // X0 X1 X2 U V G R P HP XT
+    void *img[12];         // X0 X1 Y0 Y1 U V G R P0 P1 HP XT
     void *BT, *ZK;
     double *part, *zpart;
     unsigned *bar;
     DevOut *dout, *hout;
-    double *a_host;    // a in FP64 on the host (for L of grad g)
-    int TH, tiles_x, tiles_y, ntiles;
+    double *a_host;        // a in FP64 on the host (for L of grad g)
+    int MR, Kp, nx, ny, nstrips;
+    long long *trace;      // optional barrier trace (2 * trace_cap values)
+    int trace_cap;
     cudaEvent_t ev0, ev1;  // bracket the cooperative launch on the problem's stream
     float last_ms;
 };
@@ -66,28 +66,21 @@ static Ctx<T> make_ctx(const adp_problem *p)
 {
     Ctx<T> c;
     const adp_params &q = p->prm;
-    c.C = q.C; c.H = q.H; c.W = q.W; c.K = q.K; c.r = (q.K - 1) / 2; c.h = c.r > 1 ? c.r : 1;
-    c.TH = p->TH; c.tiles_x = p->tiles_x; c.tiles_y = p->tiles_y; c.ntiles = p->ntiles;
+    c.C = q.C; c.H = q.H; c.W = q.W; c.K = q.K; c.r = (q.K - 1) / 2; c.Kp = p->Kp;
+    c.nx = p->nx; c.ny = p->ny; c.nstrips = p->nstrips;
+    c.PA = 32 + 2 * c.r; c.RA = p->MR + c.Kp - 1;
+    c.trace = p->trace; c.trace_cap = p->trace_cap;
     c.HW = (long long)q.H * q.W; c.N = c.HW * q.C;
     c.reg = q.reg; c.alpha = q.alpha; c.rp = q.reg_param; c.beta = q.beta; c.w0 = q.sobolev_w0;
     c.ddphi_max = q.reg == ADP_REG_QUAD ? 1.0 : 1.0 / q.reg_param;
     c.y = (const T *)p->y; c.a = (const T *)p->a;
-    T **im[10] = {&c.X0, &c.X1, &c.X2, &c.U, &c.V, &c.G, &c.R, &c.P, &c.HP, &c.XT};
-    for (int i = 0; i < 10; ++i) *im[i] = (T *)p->img[i];
+    T **im[12] = {&c.X0, &c.X1, &c.Y0, &c.Y1, &c.U, &c.V, &c.G, &c.R, &c.P0, &c.P1, &c.HP, &c.XT};
+    for (int i = 0; i < 12; ++i) *im[i] = (T *)p->img[i];
     c.BT = (T *)p->BT; c.ZK = (T *)p->ZK;
     c.part = p->part; c.zpart = p->zpart; c.bar = p->bar; c.out = p->dout;
-    double to = q.wait_timeout_s > 0 ? q.wait_timeout_s : 2.0;
+    const double to = q.wait_timeout_s > 0 ? q.wait_timeout_s : 2.0;
     c.timeout_ns = (long long)(to * 1e9);
     return c;
-}
-
-template <typename T>
-static size_t smem_bytes(int TH, int K)
-{
-    const int r = (K - 1) / 2, h = r > 1 ? r : 1;
-    const size_t halo = (size_t)(TH + 2 * h) * (32 + 2 * h);
-    const size_t elems = 2 * halo + (size_t)(TH + 2) * 34 + 2 * (size_t)TH * 32 + (size_t)K * K;
-    return elems * sizeof(T);
 }
 
 template <typename T>
@@ -95,12 +88,12 @@ static adp_status launch(adp_problem *p, Job<T> &jb)
 {
     Ctx<T> cx = make_ctx<T>(p);
     CK(cudaSetDevice(p->device));
-    CK(cudaMemsetAsync(p->bar, 0, 2 * sizeof(unsigned), p->stream));
+    CK(cudaMemsetAsync(p->bar, 0, sizeof(unsigned), p->stream));
     CK(cudaMemsetAsync(p->dout, 0, sizeof(DevOut), p->stream));
     void *args[] = {(void *)&cx, (void *)&jb};
     const void *fn = std::is_same<T, float>::value ? kernel_f32() : kernel_f64();
     CK(cudaEventRecord(p->ev0, p->stream));
-    CK(cudaLaunchCooperativeKernel(fn, dim3(p->grid), dim3(NT), args, p->smem, p->stream));
+    CK(cudaLaunchCooperativeKernel(fn, dim3(p->grid), dim3(32 * p->nw), args, p->smem, p->stream));
     CK(cudaEventRecord(p->ev1, p->stream));
     CK(cudaMemcpyAsync(p->hout, p->dout, sizeof(DevOut), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
@@ -110,12 +103,6 @@ static adp_status launch(adp_problem *p, Job<T> &jb)
     if (st == ST_NONFINITE) return set_err(ADP_ENONFINITE, "non-finite value in a reduction%s", "", 0);
     if (st != ST_OK) return set_err(ADP_ECUDA, "unexpected device status%s %lld", "", st);
     return ADP_OK;
-}
-
-template <typename T>
-static adp_status run(adp_problem *p, Job<T> jb)
-{
-    return launch<T>(p, jb);
 }
 
 static adp_status dispatch_job(adp_problem *p, int mode, const void *b, const void *x, void *xo, const void *v,
@@ -128,14 +115,14 @@ static adp_status dispatch_job(adp_problem *p, int mode, const void *b, const vo
         j.v = (const float *)v; j.q = (float *)q; j.z = (float *)z; j.bio = (float *)bio;
         j.eps = eps; j.delta = delta; j.max_iters = max_iters;
         if (mi) j.maid = *mi;
-        return run<float>(p, j);
+        return launch<float>(p, j);
     }
     Job<double> j{};
     j.mode = mode; j.b = (const double *)b; j.x = (const double *)x; j.xo = (double *)xo;
     j.v = (const double *)v; j.q = (double *)q; j.z = (double *)z; j.bio = (double *)bio;
     j.eps = eps; j.delta = delta; j.max_iters = max_iters;
     if (mi) j.maid = *mi;
-    return run<double>(p, j);
+    return launch<double>(p, j);
 }
 
 extern "C" {
@@ -162,7 +149,7 @@ void adp_problem_destroy(adp_problem *p)
     if (!p) return;
     cudaSetDevice(p->device);
     cudaStreamSynchronize(p->stream);
-    void *ptrs[] = {p->y, p->a, p->BT, p->ZK, p->part, p->zpart, p->bar, p->dout};
+    void *ptrs[] = {p->y, p->a, p->BT, p->ZK, p->part, p->zpart, p->bar, p->dout, p->trace};
     for (void *q : ptrs) if (q) cudaFree(q);
     for (void *q : p->img) if (q) cudaFree(q);
     if (p->hout) cudaFreeHost(p->hout);
@@ -192,11 +179,11 @@ adp_status adp_problem_create(const adp_params *prm, const void *y, const void *
     p->prm = q;
     p->stream = (cudaStream_t)stream;
     p->esize = q.prec == ADP_F32 ? sizeof(float) : sizeof(double);
-    p->TH = (q.prec == ADP_F32 ? Cfg<float>::MR : Cfg<double>::MR) * NW;
-    p->tiles_x = (q.W + 31) / 32;
-    p->tiles_y = (q.H + p->TH - 1) / p->TH;
-    p->ntiles = q.C * p->tiles_x * p->tiles_y;
-    p->smem = q.prec == ADP_F32 ? smem_bytes<float>(p->TH, q.K) : smem_bytes<double>(p->TH, q.K);
+    p->MR = q.prec == ADP_F32 ? Cfg<float>::MR : Cfg<double>::MR;
+    p->Kp = round_up(q.K, q.prec == ADP_F32 ? Cfg<float>::PC : Cfg<double>::PC);
+    p->nx = (q.W + 31) / 32;
+    p->ny = (q.H + p->MR - 1) / p->MR;
+    p->nstrips = q.C * p->nx * p->ny;
 
     adp_status st = ADP_OK;
 #define CKC(call)                                                                            \
@@ -214,38 +201,55 @@ adp_status adp_problem_create(const adp_params *prm, const void *y, const void *
     int nsm = 0, maxsmem = 0;
     CKC(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
     CKC(cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
-    // static shared memory of the kernel is small (< 1 KB); keep a margin
-    if (p->smem + 1024 > (size_t)maxsmem) {
-        adp_problem_destroy(p);
-        return set_err(ADP_EINVAL, "kernel too large for shared memory%s (%lld bytes)", "", (long long)p->smem);
+    // warps per CTA: as many as shared memory allows (the kernel's static shared
+    // memory is below 5 KB; keep that margin)
+    int w_elems = 0, warp_elems = 0, total = 0;
+    int nw = MAXNW;
+    for (; nw >= 1; --nw) {
+        if (q.prec == ADP_F32) smem_layout<float>(q.C, q.K, nw, w_elems, warp_elems, total);
+        else smem_layout<double>(q.C, q.K, nw, w_elems, warp_elems, total);
+        if ((size_t)total * p->esize + 5 * 1024 <= (size_t)maxsmem) break;
     }
+    if (nw < 1) {
+        adp_problem_destroy(p);
+        return set_err(ADP_EINVAL, "kernel too large for shared memory%s (K = %lld)", "", q.K);
+    }
+    p->nw = nw;
+    p->smem = (size_t)total * p->esize;
     const void *kfn = q.prec == ADP_F32 ? kernel_f32() : kernel_f64();
     CKC(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem));
     int occ = 0;
-    CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, NT, p->smem));
+    CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, 32 * nw, p->smem));
     if (occ < 1) {
         adp_problem_destroy(p);
         return set_err(ADP_EINVAL, "kernel cannot be resident%s", "", 0);
     }
-    long long maxgrid = (long long)occ * nsm;
-    p->grid = (int)(p->ntiles < maxgrid ? p->ntiles : maxgrid);
+    // grid: first spread the strips over the SMs (one CTA per SM, one strip per
+    // warp); beyond that add CTAs up to the co-residency limit
+    const long long maxgrid = (long long)occ * nsm;
+    long long grid;
+    if (p->nstrips <= (long long)nsm * nw) grid = p->nstrips < nsm ? p->nstrips : nsm;
+    else grid = ((long long)p->nstrips + nw - 1) / nw;
+    if (grid > maxgrid) grid = maxgrid;
+    if (grid > GT_MAX) grid = GT_MAX;   // staging buffer of the grid totals
+    p->grid = (int)grid;
 
     const size_t N = (size_t)q.C * q.H * q.W, KK = (size_t)q.C * q.K * q.K;
     CKC(cudaMalloc(&p->y, N * p->esize));
     CKC(cudaMalloc(&p->a, KK * p->esize));
-    for (int i = 0; i < 10; ++i) CKC(cudaMalloc(&p->img[i], N * p->esize));
+    for (int i = 0; i < 12; ++i) CKC(cudaMalloc(&p->img[i], N * p->esize));
     CKC(cudaMalloc(&p->BT, KK * p->esize));
     CKC(cudaMalloc(&p->ZK, KK * p->esize));
     CKC(cudaMalloc((void **)&p->part, (size_t)NSLOT * p->grid * sizeof(double)));
-    CKC(cudaMalloc((void **)&p->zpart, (size_t)p->grid * KK * sizeof(double)));
-    CKC(cudaMalloc((void **)&p->bar, 2 * sizeof(unsigned)));
+    CKC(cudaMalloc((void **)&p->zpart, (size_t)p->grid * p->nw * KK * sizeof(double)));
+    CKC(cudaMalloc((void **)&p->bar, sizeof(unsigned)));
     CKC(cudaMalloc((void **)&p->dout, sizeof(DevOut)));
     CKC(cudaMallocHost((void **)&p->hout, sizeof(DevOut)));
     CKC(cudaEventCreate(&p->ev0));
     CKC(cudaEventCreate(&p->ev1));
     CKC(cudaMemcpyAsync(p->y, y, N * p->esize, cudaMemcpyDeviceToDevice, p->stream));
     CKC(cudaMemcpyAsync(p->a, a, KK * p->esize, cudaMemcpyDeviceToDevice, p->stream));
-    for (int i = 0; i < 10; ++i) CKC(cudaMemsetAsync(p->img[i], 0, N * p->esize, p->stream));
+    for (int i = 0; i < 12; ++i) CKC(cudaMemsetAsync(p->img[i], 0, N * p->esize, p->stream));
     p->a_host = (double *)malloc(KK * sizeof(double));
     if (!p->a_host) { adp_problem_destroy(p); return set_err(ADP_ENOMEM, "host allocation failed%s", "", 0); }
     if (q.prec == ADP_F32) {
@@ -380,6 +384,33 @@ adp_status adp_maid_step(adp_problem *p, adp_maid_state *s, void *b, void *x, vo
 
 long long adp_conv_passes_last(adp_problem *p) { return p ? p->hout->conv_passes : -1; }
 int adp_grid_size(adp_problem *p) { return p ? p->grid : -1; }
+int adp_warps_per_cta(adp_problem *p) { return p ? p->nw : -1; }
 double adp_last_kernel_ms(adp_problem *p) { return p ? (double)p->last_ms : -1.0; }
+
+adp_status adp_trace_enable(adp_problem *p, int cap)
+{
+    if (!p || cap < 0) return set_err(ADP_EINVAL, "invalid trace request%s", "", 0);
+    CK(cudaSetDevice(p->device));
+    CK(cudaStreamSynchronize(p->stream));
+    if (p->trace) { CK(cudaFree(p->trace)); p->trace = nullptr; }
+    p->trace_cap = 0;
+    if (cap > 0) {
+        cudaError_t e = cudaMalloc((void **)&p->trace, (size_t)2 * cap * sizeof(long long));
+        if (e != cudaSuccess) return set_err(ADP_ENOMEM, "%s (code %lld)", cudaGetErrorString(e), (long long)e);
+        CK(cudaMemsetAsync(p->trace, 0, (size_t)2 * cap * sizeof(long long), p->stream));
+        p->trace_cap = cap;
+    }
+    return ADP_OK;
+}
+
+int adp_trace_read(adp_problem *p, long long *host_out, int cap)
+{
+    if (!p || !host_out || !p->trace) return -1;
+    int n = p->hout->barriers < p->trace_cap ? p->hout->barriers : p->trace_cap;
+    if (n > cap) n = cap;
+    if (n > 0 && cudaMemcpy(host_out, p->trace, (size_t)2 * n * sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return -1;
+    return n;
+}
 
 } // extern "C"

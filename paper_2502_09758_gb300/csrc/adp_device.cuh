@@ -1,7 +1,7 @@
-// Device building blocks of libadp: tile geometry, halo loaders, the
-// register-blocked direct correlation, deterministic FP64 reductions and the
-// bounded grid barrier, plus the launch records (Ctx, Job) shared with the host
-// code in adp.cu.
+// Device building blocks of libadp: strip geometry, asynchronous halo loaders,
+// the register-blocked direct correlation, deterministic FP64 reductions and
+// the bounded grid barrier, plus the launch records (Ctx, Job) shared with the
+// host code in adp.cu.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -9,17 +9,17 @@
 
 namespace adp {
 
-constexpr int NW = 4;              // warps per CTA
-constexpr int NT = 32 * NW;        // threads per CTA
+constexpr int MAXNW = 8;           // most warps per CTA
 constexpr int MAXC = 64;           // channels supported (per-channel step cache)
 constexpr int KMAX = 63;           // largest odd kernel size supported
 constexpr int NSLOT = 8;           // scalar reduction slots
+constexpr int QB = 8;              // lag columns per lane in the kernel-gradient correlation
 
-// Rows of outputs per thread: each warp owns a 32-column x MR-row strip, the
-// CTA stacks NW strips, so a tile is 32 x (MR*NW).
+// Output rows per thread (a warp owns a strip of 32 columns x MR rows) and
+// kernel rows per correlation chunk.
 template <typename T> struct Cfg;
-template <> struct Cfg<float>  { static constexpr int MR = 8; };
-template <> struct Cfg<double> { static constexpr int MR = 4; };
+template <> struct Cfg<float>  { static constexpr int MR = 8, PC = 16; };
+template <> struct Cfg<double> { static constexpr int MR = 4, PC = 8; };
 
 // Status words shared with the host (values equal adp_status).
 enum : int { ST_OK = 0, ST_NONFINITE = 4, ST_NOCONV = 5, ST_LSFAIL = 6, ST_TIMEOUT = 7 };
@@ -33,7 +33,10 @@ struct DevOut {
     int accepted, rounds, trials, ll_iters, ll_capped, cg_capped, k, pad;
     double eps, delta, step;
     long long conv_passes;       // number of full-image convolution passes executed
+    int barriers, pad2;          // grid barriers executed by CTA 0
 };
+
+__host__ __device__ constexpr int round_up(int a, int m) { return (a + m - 1) / m * m; }
 
 __device__ __forceinline__ int wrapi(int i, int n)
 {
@@ -55,16 +58,9 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
     return v;
 }
 
-__device__ __forceinline__ unsigned atom_add_acqrel_u32(unsigned *p, unsigned v)
+__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v)
 {
-    unsigned old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-
-__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ int ld_volatile_i32(const int *p)
@@ -72,40 +68,33 @@ __device__ __forceinline__ int ld_volatile_i32(const int *p)
     return *(const volatile int *)p;
 }
 
-// Grid-wide barrier for a cooperative launch.  Thread 0 of each CTA arrives on
-// a counter; the last arrival resets it and bumps the generation word the
-// others spin on.  Every spin is bounded: after timeout_ns, or as soon as any
-// CTA has raised a status, the waiter records ST_TIMEOUT (if nothing else was
-// recorded) and returns false, and the caller unwinds.  The host clears the two
-// words before every launch.
-__device__ __forceinline__ bool grid_sync(unsigned *bar, int *status, long long timeout_ns, int *s_flag)
+// Grid-wide barrier for a cooperative launch.  Thread 0 of each CTA adds one
+// to a monotonic arrival counter with release semantics and spins (acquire)
+// until the counter reaches epoch * gridDim.x; the CTA's other threads are
+// ordered by bar.sync on both sides.  The host zeroes the counter before each
+// launch.  Every spin is bounded: after timeout_ns, or as soon as a CTA has
+// raised a status, the waiter records ST_TIMEOUT (unless something else was
+// recorded) and returns false, and the caller unwinds.
+__device__ __forceinline__ bool grid_sync(unsigned *count, unsigned epoch, int *status, long long timeout_ns,
+                                          int *s_flag)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned *count = bar, *gen = bar + 1;
-        const unsigned g = ld_acquire_u32(gen);
-        __threadfence();
-        const unsigned prev = atom_add_acqrel_u32(count, 1u);
-        if (prev == gridDim.x - 1) {
-            *(volatile unsigned *)count = 0u;
-            __threadfence();
-            st_release_u32(gen, g + 1u);
-        } else {
-            const uint64_t t0 = globaltimer_ns();
-            unsigned spins = 0;
-            while (ld_acquire_u32(gen) == g) {
-                if ((++spins & 63u) == 0u) {
-                    if (ld_volatile_i32(status) != ST_OK) { ok = 0; break; }
-                    if ((long long)(globaltimer_ns() - t0) > timeout_ns) {
-                        atomicCAS(status, ST_OK, ST_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
+        const unsigned target = epoch * gridDim.x;
+        red_release_add_u32(count, 1u);
+        const uint64_t t0 = globaltimer_ns();
+        unsigned spins = 0;
+        while (ld_acquire_u32(count) < target) {
+            if ((++spins & 255u) == 0u) {
+                if (ld_volatile_i32(status) != ST_OK) { ok = 0; break; }
+                if ((long long)(globaltimer_ns() - t0) > timeout_ns) {
+                    atomicCAS(status, ST_OK, ST_TIMEOUT);
+                    ok = 0;
+                    break;
                 }
             }
         }
-        __threadfence();
         if (ok && ld_volatile_i32(status) != ST_OK) ok = 0;
         *s_flag = ok;
     }
@@ -122,7 +111,7 @@ __device__ __forceinline__ double warp_sum(double v)
 }
 
 // Deterministic CTA sum; every thread returns the same value.  `red` is a
-// shared array of NW doubles.
+// shared array of MAXNW doubles.
 __device__ __forceinline__ double block_sum(double v, double *red)
 {
     v = warp_sum(v);
@@ -130,80 +119,151 @@ __device__ __forceinline__ double block_sum(double v, double *red)
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     double t = 0.0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) t += red[w];
+    const int nw = blockDim.x >> 5;
+    for (int w = 0; w < nw; ++w) t += red[w];
     return t;
 }
 
-// Sum of part[0..n) in a fixed order, computed by every CTA identically (the
-// values come from other CTAs, so they are read through L2).
-__device__ __forceinline__ double grid_total(const double *part, int n, double *bcast)
+// Grid totals.  Every CTA sums part[0..n) in the same fixed order (lane l of
+// warp 0 takes entries l, l+32, ... and the lanes are combined by the shuffle
+// tree), so all CTAs obtain identical bits.  The values come from other CTAs;
+// warp 0 stages them into shared memory with asynchronous copies (one round
+// trip through L2) in grid_issue, and grid_finish waits and sums, so callers
+// can overlap the copies with other work without holding registers.
+constexpr int GT_MAX = 512;          // largest grid the staging buffer holds
+
+__device__ __forceinline__ void cp_async8(double *dst, const double *src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
+}
+
+// warp 0 only
+__device__ __forceinline__ void grid_issue(const double *part, int n, double *sbuf)
+{
+    for (int i = threadIdx.x & 31; i < n; i += 32) cp_async8(sbuf + i, part + i);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// warp 0 only; lane 0 returns the total
+__device__ __forceinline__ double grid_finish(int n, const double *sbuf)
+{
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    double s = 0.0;
+    for (int i = threadIdx.x & 31; i < n; i += 32) s += sbuf[i];
+    return warp_sum(s);
+}
+
+__device__ __forceinline__ double grid_total(const double *part, int n, double *sbuf, double *bcast)
 {
     __syncthreads();
     if (threadIdx.x < 32) {
-        double v = 0.0;
-        for (int i = threadIdx.x; i < n; i += 32) v += __ldcg(part + i);
-        v = warp_sum(v);
-        if (threadIdx.x == 0) *bcast = v;
+        grid_issue(part, n, sbuf);
+        const double s = grid_finish(n, sbuf);
+        if (threadIdx.x == 0) *bcast = s;
     }
     __syncthreads();
     return *bcast;
 }
 
-// Fill s[ii*pitch + jj] (ii < rows, jj < cols <= 128) with f(global index of
-// pixel (wrap(r0+ii), wrap(c0+jj)) of the channel starting at cbase).
-template <typename T, typename F>
-__device__ __forceinline__ void load_tile(T *s, int pitch, int rows, int cols, int H, int W,
-                                          long long cbase, int r0, int c0, F f)
+// ------------------------------------------------------------ async copies
+__device__ __forceinline__ void cp_async(float *dst, const float *src)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int gj[4];
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async(double *dst, const double *src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
+// One warp stages rows x cols (cols <= 96) of the periodic image channel at
+// cbase into s (row pitch `pitch`): s[ii][jj] = src[wrap(r0+ii), wrap(c0+jj)].
+// Asynchronous; complete with cp_async_wait_all() and __syncwarp().
+template <typename T>
+__device__ __forceinline__ void warp_stage(T *s, int pitch, int rows, int cols, const T *src, long long cbase,
+                                           int r0, int c0, int H, int W, int lane)
+{
+    int gj[3];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) gj[u] = wrapi(c0 + lane + 32 * u, W);
-    for (int ii = warp; ii < rows; ii += NW) {
-        const long long rowbase = cbase + (long long)wrapi(r0 + ii, H) * W;
+    for (int u = 0; u < 3; ++u) gj[u] = wrapi(c0 + lane + 32 * u, W);
+    int gi = wrapi(r0, H);
+    for (int ii = 0; ii < rows; ++ii) {
+        const T *rowp = src + cbase + (long long)gi * W;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 3; ++u) {
             const int jj = lane + 32 * u;
-            if (jj < cols) s[ii * pitch + jj] = f(rowbase + gj[u]);
+            if (jj < cols) cp_async(s + ii * pitch + jj, rowp + gj[u]);
         }
+        if (++gi == H) gi = 0;
     }
 }
 
-// Register-blocked direct correlation of one 1 x MR output strip:
-//   acc[m] += sum_{p<K, q<K} w[p*K + q] * s[(li0 + m + p)*pitch + lj + q]
-// For each kernel column q the MR-row window slides down the column through a
-// ring of registers: one new shared load and one broadcast weight per MR FMAs.
-template <typename T, int MR>
-__device__ __forceinline__ void corr_strip(const T *__restrict__ s, int pitch, const T *__restrict__ w,
-                                           int K, int li0, int lj, T (&acc)[MR])
+// Register-blocked direct correlation of one 1 x MR output column strip:
+//   acc[m] += sum_{q<K} sum_{p<Kq} wt[q*Kq + p] * s[(m + p)*pitch + lj + q]
+// with the kernel stored column-major (wt[q][p], p contiguous) and its rows
+// zero-padded to Kq, a multiple of PC.  The work is cut into chunks of PC
+// kernel rows of one kernel column; a chunk needs PC + MR - 1 values of the
+// thread's tile column and PC weights (vector loads, broadcast to the warp),
+// which are loaded into registers one chunk ahead of the MR x PC FMAs that use
+// them, so shared-memory latency overlaps arithmetic.
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using V = float4; static constexpr int L = 4; };
+template <> struct Vec4<double> { using V = double2; static constexpr int L = 2; };
+
+template <typename T, int PC>
+__device__ __forceinline__ void load_wchunk(const T *__restrict__ wq, T (&wv)[PC])
 {
-    for (int q = 0; q < K; ++q) {
-        const T *col = s + li0 * pitch + lj + q;
-        const T *wq = w + q;
-        T ring[MR];
+    using V = typename Vec4<T>::V;
+    constexpr int L = Vec4<T>::L;
+    const V *p = reinterpret_cast<const V *>(wq);
 #pragma unroll
-        for (int m = 0; m < MR - 1; ++m) ring[m] = col[m * pitch];
-        int p0 = 0;
-        for (; p0 + MR <= K; p0 += MR) {
-#pragma unroll
-            for (int u = 0; u < MR; ++u) {
-                ring[(MR - 1 + u) % MR] = col[(p0 + u + MR - 1) * pitch];
-                const T wv = wq[(p0 + u) * K];
-#pragma unroll
-                for (int m = 0; m < MR; ++m) acc[m] = fma(wv, ring[(m + u) % MR], acc[m]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < MR; ++u) {
-            if (p0 + u < K) {
-                ring[(MR - 1 + u) % MR] = col[(p0 + u + MR - 1) * pitch];
-                const T wv = wq[(p0 + u) * K];
-#pragma unroll
-                for (int m = 0; m < MR; ++m) acc[m] = fma(wv, ring[(m + u) % MR], acc[m]);
-            }
-        }
+    for (int i = 0; i < PC / L; ++i) {
+        const V v = p[i];
+        if constexpr (L == 4) { wv[4 * i] = v.x; wv[4 * i + 1] = v.y; wv[4 * i + 2] = v.z; wv[4 * i + 3] = v.w; }
+        else { wv[2 * i] = v.x; wv[2 * i + 1] = v.y; }
     }
+}
+
+template <typename T, int MR, int PC>
+__device__ __forceinline__ void corr_strip(const T *__restrict__ s, int pitch, const T *__restrict__ wt,
+                                           int K, int Kq, int lj, T (&acc)[MR])
+{
+    constexpr int NX = PC + MR - 1;
+    T xa[NX], wa[PC], xb[NX], wb[PC];
+    int q = 0, p0 = 0;
+    auto load = [&](T (&xv)[NX], T (&wv)[PC]) {
+        const T *col = s + p0 * pitch + lj + q;
+#pragma unroll
+        for (int i = 0; i < NX; ++i) xv[i] = col[i * pitch];
+        load_wchunk<T, PC>(wt + q * Kq + p0, wv);
+        p0 += PC;
+        if (p0 == Kq) { p0 = 0; ++q; }
+    };
+    auto comp = [&](const T (&xv)[NX], const T (&wv)[PC]) {
+#pragma unroll
+        for (int p = 0; p < PC; ++p)
+#pragma unroll
+            for (int m = 0; m < MR; ++m) acc[m] = fma(wv[p], xv[m + p], acc[m]);
+    };
+    const int total = K * (Kq / PC);
+    load(xa, wa);
+    int ci = 0;
+    for (; ci + 2 <= total; ci += 2) {
+        load(xb, wb);
+        comp(xa, wa);
+        if (ci + 2 < total) load(xa, wa);
+        comp(xb, wb);
+    }
+    if (ci < total) comp(xa, wa);
 }
 
 // phi' and phi'' of the regularisers (reg: 0 Huber, 1 sqrt, 2 quadratic).
@@ -237,17 +297,20 @@ struct MaidIn {
 
 template <typename T>
 struct Ctx {
-    int C, H, W, K, r, h;          // h = max(r, 1)
-    int TH, tiles_x, tiles_y, ntiles;
+    int C, H, W, K, r, Kp;         // Kp: kernel rows padded to a multiple of the chunk PC
+    int nx, ny, nstrips;           // strips: nx per row band, ny bands per channel
+    int PA, RA;                    // halo-r tile pitch (32 + 2r) and rows (MR + Kp - 1)
+    long long *trace;              // optional: barrier timestamps of CTA 0 (arrive, leave)
+    int trace_cap;
     long long N, HW;
     int reg;
     double alpha, rp, beta, w0, ddphi_max;
     const T *y, *a;                // data and the kernel of A (library copies)
-    T *X0, *X1, *X2, *U, *V, *G, *R, *P, *HP, *XT;   // images
+    T *X0, *X1, *Y0, *Y1, *U, *V, *G, *R, *P0, *P1, *HP, *XT;   // images
     T *BT, *ZK;                    // kernels
     double *part;                  // NSLOT x grid
-    double *zpart;                 // grid x C*K*K
-    unsigned *bar;                 // barrier words {count, generation}
+    double *zpart;                 // (grid * warps) x C*K*K
+    unsigned *bar;                 // barrier arrival counter
     DevOut *out;
     long long timeout_ns;
 };
@@ -266,5 +329,17 @@ struct Job {
     int max_iters, flag;
     MaidIn maid;
 };
+
+// Shared-memory footprint (elements of T) of one CTA with nw warps.
+template <typename T>
+__host__ __device__ inline void smem_layout(int C, int K, int nw, int &w_elems, int &warp_elems, int &total)
+{
+    constexpr int MR = Cfg<T>::MR;
+    const int r = (K - 1) / 2, Kp = round_up(K, Cfg<T>::PC);
+    const int PA = 32 + 2 * r, RA = MR + Kp - 1;
+    w_elems = round_up(2 * C * Kp * K, 4);                   // flipped and as-stored kernels
+    warp_elems = round_up(2 * RA * PA + 2 * (MR + 2) * 34, 4);   // two halo-r tiles, two halo-1 tiles
+    total = w_elems + nw * warp_elems;
+}
 
 } // namespace adp

@@ -2,10 +2,16 @@
 // member function and the cooperative kernel that runs one program of phases.
 // Included by the per-precision translation units adp_f32.cu and adp_f64.cu.
 //
+// Work decomposition: a strip is 32 columns x MR rows of one channel.  Strips
+// are dealt to warps warp-major (strip s goes to warp s mod (grid * warps) in
+// the order warp*grid + cta, so consecutive strips land on different SMs).  A
+// warp stages its strip's input with a periodic halo into its own shared
+// memory tiles with cp.async, then runs the register-blocked correlation.
+//
 // Convolution geometry (Eq. 2.4): (B x)[c,i,j] = sum_{p,q} b[c,p,q] x[c,i-p+r,j-q+r].
-// A tile of 32 x TH outputs loads its input with an r-pixel periodic halo into
-// shared memory (origin at (row0-r, col0-r)); then B x is the correlation of the
-// tile with the flipped kernel and B^T z the correlation with b itself.
+// With the tile origin at (row0-r, col0-r), B x is the correlation of the tile
+// with the flipped kernel and B^T z the correlation with b as stored; both
+// orientations are kept in shared memory, rows zero-padded to Kp.
 #pragma once
 
 #include "adp_device.cuh"
@@ -14,36 +20,46 @@ namespace adp {
 
 template <typename T>
 struct Eng {
+    static constexpr int MR = Cfg<T>::MR;
+    static constexpr int EWB = 8;  // element-wise phases: loads issued per batch per thread
     const Ctx<T> &cx;
-    T *sA, *sB, *sC, *sU, *sV, *sw;
-    int pitch;                     // of sA/sB: 32 + 2h
-    double *red, *bcast, *tau;
+    T *wF, *wT;                    // CTA: flipped / as-stored kernels, C x K x Kp (column-major)
+    T *hA, *hB, *t1, *t2;          // this warp's tiles: two halo-r, two halo-1 (pitch 34)
+    double *red, *bcast, *tau, *gbuf;
     int *sflag;
-    int lane, warp, tid;
-    bool alive;                    // false once a barrier gave up
+    int lane, warp, tid, nw, gw, TW;
+    unsigned epoch;                // barriers passed so far (same in every thread)
+    bool alive;                    // false once a barrier gave up or a status was raised
 
-    __device__ Eng(const Ctx<T> &c, unsigned char *smem, double *red_, double *bcast_, double *tau_, int *sflag_)
-        : cx(c), red(red_), bcast(bcast_), tau(tau_), sflag(sflag_), alive(true)
+    __device__ Eng(const Ctx<T> &c, unsigned char *smem, double *red_, double *bcast_, double *tau_, double *gbuf_,
+                   int *sflag_)
+        : cx(c), red(red_), bcast(bcast_), tau(tau_), gbuf(gbuf_), sflag(sflag_), epoch(0), alive(true)
     {
-        pitch = 32 + 2 * cx.h;
-        const int halo_elems = (cx.TH + 2 * cx.h) * pitch;
-        const int halo1 = (cx.TH + 2) * 34;
-        T *p = reinterpret_cast<T *>(smem);
-        sA = p; p += halo_elems;
-        sB = p; p += halo_elems;
-        sC = p; p += halo1;
-        sU = p; p += cx.TH * 32;
-        sV = p; p += cx.TH * 32;
-        sw = p;
         lane = threadIdx.x & 31;
         warp = threadIdx.x >> 5;
         tid = threadIdx.x;
+        nw = blockDim.x >> 5;
+        gw = warp * gridDim.x + blockIdx.x;
+        TW = gridDim.x * nw;
+        int w_elems, warp_elems, total;
+        smem_layout<T>(cx.C, cx.K, nw, w_elems, warp_elems, total);
+        T *base = reinterpret_cast<T *>(smem);
+        wF = base;
+        wT = base + cx.C * cx.Kp * cx.K;
+        hA = base + w_elems + warp * warp_elems;
+        hB = hA + cx.RA * cx.PA;
+        t1 = hB + cx.RA * cx.PA;
+        t2 = t1 + (MR + 2) * 34;
     }
 
     __device__ bool sync()
     {
         if (!alive) return false;
-        alive = grid_sync(cx.bar, &cx.out->status, cx.timeout_ns, sflag);
+        ++epoch;
+        const bool tr = cx.trace && blockIdx.x == 0 && tid == 0 && (int)epoch <= cx.trace_cap;
+        if (tr) cx.trace[2 * (epoch - 1)] = (long long)globaltimer_ns();
+        alive = grid_sync(cx.bar, epoch, &cx.out->status, cx.timeout_ns, sflag);
+        if (tr) cx.trace[2 * (epoch - 1) + 1] = (long long)globaltimer_ns();
         return alive;
     }
 
@@ -53,103 +69,124 @@ struct Eng {
         alive = false;
     }
 
-    __device__ void tile_of(int t, int &c, int &row0, int &col0) const
+    __device__ long long gstride() const { return (long long)gridDim.x * blockDim.x; }
+    __device__ long long gstart() const { return (long long)blockIdx.x * blockDim.x + tid; }
+
+    __device__ void strip_of(int s, int &c, int &row0, int &col0) const
     {
-        const int per = cx.tiles_x * cx.tiles_y;
-        c = t / per;
-        const int rem = t - c * per;
-        const int ty = rem / cx.tiles_x;
-        row0 = ty * cx.TH;
-        col0 = (rem - ty * cx.tiles_x) * 32;
+        const int per = cx.nx * cx.ny;
+        c = s / per;
+        const int rem = s - c * per;
+        const int sy = rem / cx.nx;
+        row0 = sy * MR;
+        col0 = (rem - sy * cx.nx) * 32;
     }
 
-    // weights of channel c into sw, flipped for B, as stored for B^T
-    __device__ void load_w(const T *b, int c, bool flip)
+    // both orientations of kernel b (all channels) into shared memory, stored
+    // column-major per channel: w[c][q][p], p < Kp (rows beyond K are zero)
+    __device__ void load_weights(const T *b)
     {
-        const int KK = cx.K * cx.K;
-        const T *bc = b + (long long)c * KK;
-        for (int e = tid; e < KK; e += NT) sw[e] = flip ? __ldcg(bc + (KK - 1 - e)) : __ldcg(bc + e);
+        __syncthreads();
+        const int K = cx.K, Kp = cx.Kp, KK = K * K, per = Kp * K, n = cx.C * per;
+        for (int e = tid; e < n; e += blockDim.x) {
+            const int c = e / per, rem = e - c * per, q = rem / Kp, p = rem - q * Kp;
+            T f = T(0), t = T(0);
+            if (p < K) {
+                const T *bc = b + (long long)c * KK;
+                f = __ldcg(bc + (K - 1 - p) * K + (K - 1 - q));
+                t = __ldcg(bc + p * K + q);
+            }
+            wF[e] = f;
+            wT[e] = t;
+        }
+        __syncthreads();
     }
 
-    // record the partial of this CTA in a slot and return the grid total after
-    // a barrier; all CTAs get identical bits
+    // record this CTA's partial in a slot and return the grid total after a
+    // barrier; every CTA obtains identical bits
     __device__ double reduce(double mine, int slot)
     {
         const double cta = block_sum(mine, red);
         if (tid == 0) cx.part[slot * gridDim.x + blockIdx.x] = cta;
         if (!sync()) return 0.0;
-        return grid_total(cx.part + slot * gridDim.x, gridDim.x, bcast);
+        return grid_total(cx.part + slot * gridDim.x, gridDim.x, gbuf, bcast);
     }
 
-    // ------------------------------------------------------------ conv pass
-    // One pass over all tiles: load the halo-r tile from src, correlate with
-    // the (flipped) kernel of channel c, and hand each in-image output to epi,
-    // whose return values are summed (FP32 per strip, FP64 across strips).
-    template <typename Src, typename Pre, typename Epi>
-    __device__ double conv_pass(const T *b, bool flip, Src src, Pre pre, Epi epi)
+    __device__ void stage_halo(T *dst, const T *src, long long cbase, int row0, int col0) const
     {
-        constexpr int MR = Cfg<T>::MR;
-        const int r = cx.r, K = cx.K, H = cx.H, W = cx.W;
-        double part = 0.0;
-        for (int t = blockIdx.x; t < cx.ntiles; t += gridDim.x) {
-            int c, row0, col0;
-            tile_of(t, c, row0, col0);
-            const long long cbase = (long long)c * cx.HW;
-            load_w(b, c, flip);
-            load_tile(sA, pitch, cx.TH + 2 * r, 32 + 2 * r, H, W, cbase, row0 - r, col0 - r, src);
-            pre(c, row0, col0, cbase);
-            __syncthreads();
-            T acc[MR];
+        warp_stage(dst, cx.PA, cx.RA, cx.PA, src, cbase, row0 - cx.r, col0 - cx.r, cx.H, cx.W, lane);
+    }
+
+    __device__ void stage_halo1(T *dst, const T *src, long long cbase, int row0, int col0) const
+    {
+        warp_stage(dst, 34, MR + 2, 34, src, cbase, row0 - 1, col0 - 1, cx.H, cx.W, lane);
+    }
+
+    __device__ void corr(const T *tile, bool flip, int c, T (&acc)[MR]) const
+    {
 #pragma unroll
-            for (int m = 0; m < MR; ++m) acc[m] = T(0);
-            const int li0 = warp * MR;
-            corr_strip<T, MR>(sA, pitch, sw, K, li0, lane, acc);
-            T s = T(0);
+        for (int m = 0; m < MR; ++m) acc[m] = T(0);
+        const T *w = (flip ? wF : wT) + c * cx.Kp * cx.K;
+        corr_strip<T, MR, Cfg<T>::PC>(tile, cx.PA, w, cx.K, cx.Kp, lane, acc);
+    }
+
+    // One convolution pass over all strips.  stage() issues the async copies of
+    // the strip (halo-r input into hA, extra tiles as needed); fetch(g) loads a
+    // per-pixel operand of the epilogue, issued while the copies are in flight;
+    // prep() runs on the staged tiles before the correlation; epi() consumes
+    // each in-image output (with its fetched operand) and returns its share of a
+    // reduction (FP32 per strip, FP64 across strips).
+    template <typename Stage, typename Fetch, typename Prep, typename Epi>
+    __device__ double pass(bool flip, Stage stage, Fetch fetch, Prep prep, Epi epi)
+    {
+        double part = 0.0;
+        for (int s = gw; s < cx.nstrips; s += TW) {
+            int c, row0, col0;
+            strip_of(s, c, row0, col0);
+            const long long cbase = (long long)c * cx.HW;
+            stage(c, row0, col0, cbase);
             const int gj = col0 + lane;
+            T aux[MR];
 #pragma unroll
             for (int m = 0; m < MR; ++m) {
-                const int gi = row0 + li0 + m;
-                if (gi < H && gj < W) s += epi(c, li0 + m, lane, cbase + (long long)gi * W + gj, acc[m]);
+                const int gi = row0 + m;
+                aux[m] = (gi < cx.H && gj < cx.W) ? fetch(cbase + (long long)gi * cx.W + gj) : T(0);
             }
-            part += (double)s;
-            __syncthreads();
+            cp_async_wait_all();
+            __syncwarp();
+            prep(c, row0, col0, cbase);
+            __syncwarp();
+            T acc[MR];
+            corr(hA, flip, c, acc);
+            T sum = T(0);
+#pragma unroll
+            for (int m = 0; m < MR; ++m) {
+                const int gi = row0 + m;
+                if (gi < cx.H && gj < cx.W) sum += epi(c, m, cbase + (long long)gi * cx.W + gj, acc[m], aux[m]);
+            }
+            part += (double)sum;
+            __syncwarp();
         }
         return part;
     }
 
-    // ------------------------------------------------------------ helpers
-    __device__ long long gstride() const { return (long long)gridDim.x * NT; }
-    __device__ long long gstart() const { return (long long)blockIdx.x * NT + tid; }
+    static __device__ T nofetch(long long) { return T(0); }
 
-    // 1/L_c for FISTA on channel c with kernel b: L_c = ||b_c||_1^2 + 8 alpha sup phi''
-    __device__ void compute_tau(const T *b)
-    {
-        const int KK = cx.K * cx.K;
-        for (int c = 0; c < cx.C; ++c) {
-            double s = 0.0;
-            for (int e = tid; e < KK; e += NT) s += fabs((double)__ldcg(b + (long long)c * KK + e));
-            const double l1 = block_sum(s, red);
-            if (tid == 0) tau[c] = 1.0 / (l1 * l1 + 8.0 * cx.alpha * cx.ddphi_max);
-        }
-        __syncthreads();
-    }
-
-    // TV gradient at interior pixel (li, lj) of a halo-1 tile s (pitch 34)
-    __device__ T tv_grad(const T *s, int li, int lj) const
+    // TV gradient at strip pixel (m, lane) of a halo-1 tile s (pitch 34)
+    __device__ T tv_grad(const T *s, int m) const
     {
         const T g = (T)cx.rp;
-        const T yc = s[(li + 1) * 34 + lj + 1];
-        const T yl = s[(li + 1) * 34 + lj], yr = s[(li + 1) * 34 + lj + 2];
-        const T yu = s[li * 34 + lj + 1], yd = s[(li + 2) * 34 + lj + 1];
-        return dphi<T>(cx.reg, yc - yl, g) - dphi<T>(cx.reg, yr - yc, g) +
-               dphi<T>(cx.reg, yc - yu, g) - dphi<T>(cx.reg, yd - yc, g);
+        const int o = (m + 1) * 34 + lane + 1;
+        const T yc = s[o];
+        return dphi<T>(cx.reg, yc - s[o - 1], g) - dphi<T>(cx.reg, s[o + 1] - yc, g) +
+               dphi<T>(cx.reg, yc - s[o - 34], g) - dphi<T>(cx.reg, s[o + 34] - yc, g);
     }
 
-    // D^T(phi''(D x) . D v) at interior pixel (li, lj); x in sx, v in sv (halo 1)
-    __device__ T tv_hess(const T *sx, const T *sv, int li, int lj) const
+    // D^T(phi''(D x) . D v) at strip pixel (m, lane); x in sx, v in sv (halo 1)
+    __device__ T tv_hess(const T *sx, const T *sv, int m) const
     {
         const T g = (T)cx.rp;
-        const int o = (li + 1) * 34 + lj + 1;
+        const int o = (m + 1) * 34 + lane + 1;
         const T xc = sx[o], vc = sv[o];
         const T wl = ddphi<T>(cx.reg, xc - sx[o - 1], g);
         const T wr = ddphi<T>(cx.reg, sx[o + 1] - xc, g);
@@ -158,142 +195,194 @@ struct Eng {
         return wl * (vc - sv[o - 1]) - wr * (sv[o + 1] - vc) + wu * (vc - sv[o - 34]) - wd * (sv[o + 34] - vc);
     }
 
-    __device__ void load_halo1(T *s, int row0, int col0, long long cbase, const T *src) const
-    {
-        load_tile(s, 34, cx.TH + 2, 34, cx.H, cx.W, cbase, row0 - 1, col0 - 1,
-                  [=](long long g) { return __ldcg(src + g); });
-    }
-
     // ------------------------------------------------------------ programs
-    // out = B x (flip) or B^T x
     __device__ void apply(const T *b, const T *x, T *out, bool transpose)
     {
-        conv_pass(b, !transpose, [=](long long g) { return __ldcg(x + g); },
-                  [](int, int, int, long long) {},
-                  [=](int, int, int, long long g, T v) { out[g] = v; return T(0); });
+        load_weights(b);
+        pass(!transpose, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, x, cbase, row0, col0); },
+             nofetch, [](int, int, int, long long) {},
+             [=](int, int, long long g, T v, T) { out[g] = v; return T(0); });
     }
 
-    // U = B x - y   (first half of grad_x h)
-    __device__ void residual(const T *b, const T *x, T *U)
+    // U = B x - y (weights of b loaded)
+    __device__ void residual(const T *x, T *U)
     {
         const T *y = cx.y;
-        conv_pass(b, true, [=](long long g) { return __ldcg(x + g); },
-                  [](int, int, int, long long) {},
-                  [=](int, int, int, long long g, T v) { U[g] = v - __ldg(y + g); return T(0); });
-    }
-
-    // grad = B^T U + alpha grad J(x); optional store; returns ||grad||^2 partial
-    __device__ double grad_from_residual(const T *b, const T *U, const T *x, T *out)
-    {
-        const T al = (T)cx.alpha;
-        T *sBl = sB;
-        return conv_pass(b, false, [=](long long g) { return __ldcg(U + g); },
-                         [=](int, int row0, int col0, long long cbase) { load_halo1(sBl, row0, col0, cbase, x); },
-                         [=](int, int li, int lj, long long g, T v) {
-                             const T gr = v + al * tv_grad(sBl, li, lj);
-                             if (out) out[g] = gr;
-                             return gr * gr;
-                         });
+        pass(true, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, x, cbase, row0, col0); },
+             [=](long long g) { return __ldg(y + g); }, [](int, int, int, long long) {},
+             [=](int, int, long long g, T v, T yv) { U[g] = v - yv; return T(0); });
     }
 
     __device__ void grad_lower(const T *b, const T *x, T *out)
     {
-        residual(b, x, cx.U);
+        load_weights(b);
+        residual(x, cx.U);
         if (!sync()) return;
-        const double ss = reduce(grad_from_residual(b, cx.U, x, out), 0);
-        if (tid == 0 && blockIdx.x == 0) cx.out->gradnorm = sqrt(ss);
+        const T al = (T)cx.alpha;
+        const T *U = cx.U;
+        const double part = pass(
+            false,
+            [=](int, int row0, int col0, long long cbase) {
+                stage_halo(hA, U, cbase, row0, col0);
+                stage_halo1(t1, x, cbase, row0, col0);
+            },
+            nofetch, [](int, int, int, long long) {},
+            [=](int, int m, long long g, T v, T) {
+                const T gr = v + al * tv_grad(t1, m);
+                if (out) out[g] = gr;
+                return gr * gr;
+            });
+        const double ss = reduce(part, 0);
+        if (alive && tid == 0 && blockIdx.x == 0) cx.out->gradnorm = sqrt(ss);
     }
 
-    // out = B^T B v + alpha D^T(phi''(D x) . D v); returns <v, out> partial
-    __device__ double hess_vec(const T *b, const T *x, const T *v, T *out)
+    // out = B^T B v + alpha D^T(phi''(D x) . D v) (weights of b loaded); returns
+    // this CTA's share of <v, out>
+    __device__ double hess_vec(const T *x, const T *v, T *out)
     {
         const T al = (T)cx.alpha;
         T *U = cx.U;
-        conv_pass(b, true, [=](long long g) { return __ldcg(v + g); },
-                  [](int, int, int, long long) {},
-                  [=](int, int, int, long long g, T val) { U[g] = val; return T(0); });
+        pass(true, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, v, cbase, row0, col0); },
+             nofetch, [](int, int, int, long long) {},
+             [=](int, int, long long g, T val, T) { U[g] = val; return T(0); });
         if (!sync()) return 0.0;
-        T *sBl = sB, *sCl = sC;
-        return conv_pass(b, false, [=](long long g) { return __ldcg(U + g); },
-                         [=](int, int row0, int col0, long long cbase) {
-                             load_halo1(sBl, row0, col0, cbase, x);
-                             load_halo1(sCl, row0, col0, cbase, v);
-                         },
-                         [=](int, int li, int lj, long long g, T val) {
-                             const T hv = val + al * tv_hess(sBl, sCl, li, lj);
-                             out[g] = hv;
-                             return hv * sCl[(li + 1) * 34 + lj + 1];
-                         });
+        return pass(
+            false,
+            [=](int, int row0, int col0, long long cbase) {
+                stage_halo(hA, U, cbase, row0, col0);
+                stage_halo1(t1, x, cbase, row0, col0);
+                stage_halo1(t2, v, cbase, row0, col0);
+            },
+            nofetch, [](int, int, int, long long) {},
+            [=](int, int m, long long g, T val, T) {
+                const T hv = val + al * tv_hess(t1, t2, m);
+                out[g] = hv;
+                return hv * t2[(m + 1) * 34 + lane + 1];
+            });
     }
 
-    // FISTA from x_in (warm start) to x_out; returns updates made, sets gn
-    __device__ int lower_solve(const T *b, const T *x_in, T *x_out, double eps, int max_iters,
-                               double &gn, long long &passes)
+    // 1/L_c for FISTA on channel c with kernel b: L_c = ||b_c||_1^2 + 8 alpha sup phi''
+    __device__ void compute_tau(const T *b)
     {
-        const T *y = cx.y;
-        compute_tau(b);
-        for (long long i = gstart(); i < cx.N; i += gstride()) {
-            const T v = __ldcg(x_in + i);
-            cx.X0[i] = v;
-            cx.X1[i] = v;
+        const int KK = cx.K * cx.K;
+        for (int c = 0; c < cx.C; ++c) {
+            double s = 0.0;
+            for (int e = tid; e < KK; e += blockDim.x) s += fabs((double)__ldcg(b + (long long)c * KK + e));
+            const double l1 = block_sum(s, red);
+            if (tid == 0) tau[c] = 1.0 / (l1 * l1 + 8.0 * cx.alpha * cx.ddphi_max);
         }
+        __syncthreads();
+    }
+
+    // dst[i] = src[i] (and dst2[i] = src[i] if dst2), loads issued EWB at a time
+    __device__ void copy_img(T *dst, T *dst2, const T *src)
+    {
+        const long long N = cx.N, st = gstride();
+        for (long long base = gstart(); base < N; base += EWB * st) {
+            T v[EWB];
+#pragma unroll
+            for (int u = 0; u < EWB; ++u) { const long long i = base + u * st; v[u] = i < N ? __ldcg(src + i) : T(0); }
+#pragma unroll
+            for (int u = 0; u < EWB; ++u) {
+                const long long i = base + u * st;
+                if (i < N) { dst[i] = v[u]; if (dst2) dst2[i] = v[u]; }
+            }
+        }
+    }
+
+    // FISTA (Algorithm 1, step 1) from x_in to x_out: returns updates made.
+    // The momentum theta_{k+1} = (t_k - 1)/t_{k+1} does not depend on the data,
+    // so pass B writes both x_{k+1} and y_{k+1}.  The stopping test on
+    // ||grad_x h(y_k)|| is read one pass late: the partial sums of iteration k
+    // are fetched while pass A of iteration k+1 runs, and when the test holds
+    // y_k (still in its own buffer) is returned and that pass A is discarded.
+    __device__ int lower_solve(const T *b, const T *x_in, T *x_out, double eps, int max_iters, double &gn,
+                               long long &passes)
+    {
+        load_weights(b);
+        compute_tau(b);
+        copy_img(cx.X0, cx.Y0, x_in);
         if (!sync()) return 0;
-        T *x0 = cx.X0, *x1 = cx.X1, *x2 = cx.X2, *U = cx.U;
-        double t = 1.0, theta = 0.0;
-        int k = 0;
+        T *xp = cx.X0, *xn = cx.X1, *yc = cx.Y0, *yn = cx.Y1, *U = cx.U;
+        const T *y = cx.y;
         const T al = (T)cx.alpha;
-        T *sBl = sB;
         const double *tauc = tau;
+        const T *result = nullptr;
+        double t = 1.0;
+        bool pending = false;
+        int k = 0;
         for (;; ++k) {
-            const T th = (T)theta;
-            // phase A: U = B y_k - y, y_k = x_k + theta (x_k - x_{k-1}) formed on the fly
-            conv_pass(b, true,
-                      [=](long long g) { const T a1 = __ldcg(x1 + g); return a1 + th * (a1 - __ldcg(x0 + g)); },
-                      [](int, int, int, long long) {},
-                      [=](int, int, int, long long g, T v) { U[g] = v - __ldg(y + g); return T(0); });
+            const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+            const T thn = (T)((t - 1.0) / tn);
+            const T *ycur = yc;
+            if (pending && warp == 0) grid_issue(cx.part + ((k - 1) & 1) * gridDim.x, gridDim.x, gbuf);
+            // phase A: U = B y_k - y
+            pass(true, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, ycur, cbase, row0, col0); },
+                 [=](long long g) { return __ldg(y + g); }, [](int, int, int, long long) {},
+                 [=](int, int, long long g, T v, T yv) { U[g] = v - yv; return T(0); });
+            if (pending) {
+                if (warp == 0) {
+                    const double s = grid_finish(gridDim.x, gbuf);
+                    if (lane == 0) *bcast = s;
+                }
+                __syncthreads();
+                const double gprev = sqrt(*bcast);
+                __syncthreads();
+                if (!isfinite(gprev)) { fail(ST_NONFINITE); return k - 1; }
+                if (gprev <= eps) {        // y_{k-1} passes: keep it, drop this pass A
+                    gn = gprev;
+                    result = yn;
+                    --k;
+                    break;
+                }
+            }
             if (!sync()) return k;
-            // phase B: G = B^T U + alpha grad J(y_k); x_{k+1} = y_k - tau_c G; ||G||^2
-            const double part = conv_pass(
-                b, false, [=](long long g) { return __ldcg(U + g); },
+            // phase B: G = B^T U + alpha grad J(y_k); x_{k+1} = y_k - tau_c G;
+            // y_{k+1} = x_{k+1} + theta_{k+1} (x_{k+1} - x_k); ||G||^2
+            T *xnl = xn, *ynl = yn;
+            const T *xpl = xp;
+            const double part = pass(
+                false,
                 [=](int, int row0, int col0, long long cbase) {
-                    load_tile(sBl, 34, cx.TH + 2, 34, cx.H, cx.W, cbase, row0 - 1, col0 - 1, [=](long long g) {
-                        const T a1 = __ldcg(x1 + g);
-                        return a1 + th * (a1 - __ldcg(x0 + g));
-                    });
+                    stage_halo(hA, U, cbase, row0, col0);
+                    stage_halo1(t1, ycur, cbase, row0, col0);
                 },
-                [=](int c, int li, int lj, long long g, T v) {
-                    const T gr = v + al * tv_grad(sBl, li, lj);
-                    x2[g] = sBl[(li + 1) * 34 + lj + 1] - (T)tauc[c] * gr;
+                [=](long long g) { return __ldcg(xpl + g); }, [](int, int, int, long long) {},
+                [=](int c, int m, long long g, T v, T xpv) {
+                    const T gr = v + al * tv_grad(t1, m);
+                    const T xnv = t1[(m + 1) * 34 + lane + 1] - (T)tauc[c] * gr;
+                    xnl[g] = xnv;
+                    ynl[g] = xnv + thn * (xnv - xpv);
                     return gr * gr;
                 });
-            const double ss = reduce(part, k & 1);
-            if (!alive) return k;
+            const double cta = block_sum(part, red);
+            if (tid == 0) cx.part[(k & 1) * gridDim.x + blockIdx.x] = cta;
+            if (!sync()) return k;
             passes += 2;
-            gn = sqrt(ss);
-            if (!isfinite(gn)) { fail(ST_NONFINITE); return k; }
-            if (gn <= eps || k >= max_iters) break;
-            const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-            theta = (t - 1.0) / tn;
+            if (k >= max_iters) {          // cap: the norm of y_k is needed now
+                gn = sqrt(grid_total(cx.part + (k & 1) * gridDim.x, gridDim.x, gbuf, bcast));
+                if (!isfinite(gn)) { fail(ST_NONFINITE); return k; }
+                result = yc;
+                break;
+            }
+            pending = true;
             t = tn;
-            T *tmp = x0; x0 = x1; x1 = x2; x2 = tmp;
+            T *tmp = xp; xp = xn; xn = tmp;
+            tmp = yc; yc = yn; yn = tmp;
         }
-        const T th = (T)theta;
-        for (long long i = gstart(); i < cx.N; i += gstride()) {
-            const T a1 = __ldcg(x1 + i);
-            x_out[i] = a1 + th * (a1 - __ldcg(x0 + i));
-        }
+        copy_img(x_out, nullptr, result);
         return k;
     }
 
     // r(b) = beta (w0 ||d||^2 + ||D_h d||^2 + ||D_v d||^2), d = b - a; every
-    // CTA computes it (small); grad r into gr (may be null) by CTA 0's threads
+    // CTA computes it (it is small)
     __device__ T dker(const T *b, long long idx) const { return __ldcg(b + idx) - __ldg(cx.a + idx); }
 
     __device__ double sobolev(const T *b)
     {
         const int K = cx.K, KK = K * K;
         double s = 0.0;
-        for (int e = tid; e < cx.C * KK; e += NT) {
+        for (int e = tid; e < cx.C * KK; e += blockDim.x) {
             const int c = e / KK, pq = e - c * KK, p = pq / K, q = pq - p * K;
             const long long base = (long long)c * KK;
             const double d = (double)dker(b, base + pq);
@@ -321,27 +410,30 @@ struct Eng {
     // ell = g(x) + r(b) and ||grad g(x)||; grad g stored in cx.G
     __device__ void upper_loss(const T *b, const T *x, double &loss, double &gxn, long long &passes)
     {
-        const T *y = cx.y;
-        T *V = cx.V, *G = cx.G;
         // r(b) first: b may be rewritten by other CTAs right after the last
         // barrier of this function (the next backtracking trial)
         const double rb = sobolev(b);
-        const double pg = conv_pass(cx.a, true, [=](long long g) { return __ldcg(x + g); },
-                                    [](int, int, int, long long) {},
-                                    [=](int, int, int, long long g, T v) {
-                                        const T e = v - __ldg(y + g);
-                                        V[g] = e;
-                                        return e * e;
-                                    });
+        load_weights(cx.a);
+        const T *y = cx.y;
+        T *V = cx.V, *G = cx.G;
+        const double pg = pass(
+            true, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, x, cbase, row0, col0); },
+            [=](long long g) { return __ldg(y + g); }, [](int, int, int, long long) {},
+            [=](int, int, long long g, T v, T yv) {
+                const T e = v - yv;
+                V[g] = e;
+                return e * e;
+            });
         const double gval = reduce(pg, 2);
         if (!alive) return;
-        const double pgg = conv_pass(cx.a, false, [=](long long g) { return __ldcg(V + g); },
-                                     [](int, int, int, long long) {},
-                                     [=](int, int, int, long long g, T v) {
-                                         const T gg = T(2) * v;
-                                         G[g] = gg;
-                                         return gg * gg;
-                                     });
+        const double pgg = pass(
+            false, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, V, cbase, row0, col0); },
+            nofetch, [](int, int, int, long long) {},
+            [=](int, int, long long g, T v, T) {
+                const T gg = T(2) * v;
+                G[g] = gg;
+                return gg * gg;
+            });
         const double ggs = reduce(pgg, 3);
         if (!alive) return;
         passes += 2;
@@ -350,148 +442,241 @@ struct Eng {
         if (!isfinite(loss) || !isfinite(gxn)) fail(ST_NONFINITE);
     }
 
-    // CG on H(x, b) q = rhs from the q held in Q (zero_start: Q is taken as
-    // zero and cleared).  Returns iterations; sets res and capped.
-    __device__ int cg(const T *b, const T *x, const T *rhs, T *Q, double delta, int max_iters,
-                      bool zero_start, double &res, int &capped, long long &passes)
+    // CG (Algorithm 1, step 2) on H(x, b) q = rhs from the q held in Q
+    // (zero_start: Q is taken as zero).  The direction update p = r + beta p of
+    // iteration k is fused into the B p pass of iteration k+1 (computed on the
+    // staged halo tiles of r and the previous p).  Returns iterations.
+    __device__ int cg(const T *b, const T *x, const T *rhs, T *Q, double delta, int max_iters, bool zero_start,
+                      double &res, int &capped, long long &passes)
     {
-        T *R = cx.R, *P = cx.P, *HP = cx.HP;
+        load_weights(b);
+        T *R = cx.R, *HP = cx.HP, *U = cx.U;
+        T *pc = cx.P0, *po = cx.P1;
         double rrp = 0.0;
-        if (zero_start) {
-            for (long long i = gstart(); i < cx.N; i += gstride()) {
-                const T v = __ldcg(rhs + i);
-                Q[i] = T(0);
-                R[i] = v;
-                P[i] = v;
-                rrp += (double)v * (double)v;
-            }
-        } else {
-            hess_vec(b, x, Q, HP);
+        const long long N = cx.N, st = gstride();
+        if (!zero_start) {
+            hess_vec(x, Q, HP);
             if (!sync()) return 0;
             passes += 2;
-            for (long long i = gstart(); i < cx.N; i += gstride()) {
-                const T v = __ldcg(rhs + i) - __ldcg(HP + i);
-                R[i] = v;
-                P[i] = v;
-                rrp += (double)v * (double)v;
+        }
+        {
+            T s = T(0);
+            for (long long base = gstart(); base < N; base += EWB * st) {
+                T v[EWB];
+#pragma unroll
+                for (int u = 0; u < EWB; ++u) {
+                    const long long i = base + u * st;
+                    v[u] = i < N ? (zero_start ? __ldcg(rhs + i) : __ldcg(rhs + i) - __ldcg(HP + i)) : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < EWB; ++u) {
+                    const long long i = base + u * st;
+                    if (i < N) {
+                        if (zero_start) Q[i] = T(0);
+                        R[i] = v[u];
+                        pc[i] = v[u];
+                        s += v[u] * v[u];
+                    }
+                }
             }
+            rrp = (double)s;
         }
         double rr = reduce(rrp, 4);
         if (!alive) return 0;
         int it = 0;
         capped = 0;
+        bool first = true;
+        T beta = T(0);
+        const T al = (T)cx.alpha;
         while (sqrt(rr) > delta && it < max_iters) {
-            const double php = reduce(hess_vec(b, x, P, HP), 5);
+            // phase A: p (fused update unless first) and U = B p
+            T *pcl = pc;
+            const T *pol = po;
+            const bool fst = first;
+            const T bt = beta;
+            pass(
+                true,
+                [=](int, int row0, int col0, long long cbase) {
+                    if (fst) {
+                        stage_halo(hA, pcl, cbase, row0, col0);
+                    } else {
+                        stage_halo(hA, R, cbase, row0, col0);
+                        stage_halo(hB, pol, cbase, row0, col0);
+                    }
+                },
+                nofetch,
+                [=](int, int row0, int col0, long long cbase) {
+                    if (fst) return;
+                    const int n = cx.RA * cx.PA;
+                    for (int e = lane; e < n; e += 32) hA[e] = hA[e] + bt * hB[e];
+                    __syncwarp();
+                    const int gj = col0 + lane;
+                    for (int m = 0; m < MR; ++m) {
+                        const int gi = row0 + m;
+                        if (gi < cx.H && gj < cx.W)
+                            pcl[cbase + (long long)gi * cx.W + gj] = hA[(m + cx.r) * cx.PA + lane + cx.r];
+                    }
+                },
+                [=](int, int, long long g, T v, T) { U[g] = v; return T(0); });
+            if (!sync()) return it;
+            // phase B: HP = B^T U + alpha D^T(phi''(D x) . D p); <p, HP>
+            const double php = reduce(
+                pass(
+                    false,
+                    [=](int, int row0, int col0, long long cbase) {
+                        stage_halo(hA, U, cbase, row0, col0);
+                        stage_halo1(t1, x, cbase, row0, col0);
+                        stage_halo1(t2, pcl, cbase, row0, col0);
+                    },
+                    nofetch, [](int, int, int, long long) {},
+                    [=](int, int m, long long g, T v, T) {
+                        const T hv = v + al * tv_hess(t1, t2, m);
+                        HP[g] = hv;
+                        return hv * t2[(m + 1) * 34 + lane + 1];
+                    }),
+                5);
             if (!alive) return it;
             passes += 2;
             if (!isfinite(php)) { fail(ST_NONFINITE); return it; }
             if (!(php > 0.0)) { capped = 1; break; }
             const T a = (T)(rr / php);
-            double rn = 0.0;
-            for (long long i = gstart(); i < cx.N; i += gstride()) {
-                const T pv = __ldcg(P + i);
-                Q[i] = __ldcg(Q + i) + a * pv;
-                const T rv = __ldcg(R + i) - a * __ldcg(HP + i);
-                R[i] = rv;
-                rn += (double)rv * (double)rv;
+            T s = T(0);
+            for (long long base = gstart(); base < N; base += EWB * st) {
+                T pv[EWB], qv[EWB], rv[EWB], hv[EWB];
+#pragma unroll
+                for (int u = 0; u < EWB; ++u) {
+                    const long long i = base + u * st;
+                    if (i < N) { pv[u] = __ldcg(pcl + i); qv[u] = __ldcg(Q + i); rv[u] = __ldcg(R + i); hv[u] = __ldcg(HP + i); }
+                }
+#pragma unroll
+                for (int u = 0; u < EWB; ++u) {
+                    const long long i = base + u * st;
+                    if (i < N) {
+                        Q[i] = qv[u] + a * pv[u];
+                        const T r2 = rv[u] - a * hv[u];
+                        R[i] = r2;
+                        s += r2 * r2;
+                    }
+                }
             }
-            const double rr_new = reduce(rn, 6);
+            const double rr_new = reduce((double)s, 6);
             if (!alive) return it;
             ++it;
             if (!isfinite(rr_new)) { fail(ST_NONFINITE); return it; }
             if (sqrt(rr_new) <= delta) { rr = rr_new; break; }
-            const T be = (T)(rr_new / rr);
+            beta = (T)(rr_new / rr);
             rr = rr_new;
-            for (long long i = gstart(); i < cx.N; i += gstride()) P[i] = __ldcg(R + i) + be * __ldcg(P + i);
-            if (!sync()) return it;
+            po = pc;
+            pc = (pc == cx.P0) ? cx.P1 : cx.P0;
+            first = false;
         }
         res = sqrt(rr);
         if (res > delta) capped = 1;
         return it;
     }
 
-    // out[c,p,q] = sum_ij x[c,i-p+r,j-q+r] (B v)[c,i,j] + v[c,i-p+r,j-q+r] (B x - y)[c,i,j];
-    // z = -out (+ grad r(b) when add_r); written to zout; returns ||z||^2
-    __device__ double cross(const T *b, const T *x, const T *v, T *zout, bool negate, bool add_r,
-                            long long &passes)
+    // out[c,p,q] = sum_ij x[c,i-p+r,j-q+r] (B v)[c,i,j] + v[c,i-p+r,j-q+r] (B x - y)[c,i,j]
+    // (Algorithm 1, step 3, with the sign of Eq. 3.2: z = -out (+ grad r(b)));
+    // written to zout; returns ||zout||^2
+    __device__ double cross(const T *b, const T *x, const T *v, T *zout, bool negate, bool add_r, long long &passes)
     {
+        load_weights(b);
         const T *y = cx.y;
         T *U = cx.U, *V = cx.V;
-        constexpr int MR = Cfg<T>::MR;
         const int r = cx.r, K = cx.K, KK = K * K, H = cx.H, W = cx.W;
         const int CKK = cx.C * KK;
+        double *zp = cx.zpart + (long long)gw * CKK;
+        for (int e = lane; e < CKK; e += 32) zp[e] = 0.0;
         // phase K1: U = B v, V = B x - y
-        for (int t = blockIdx.x; t < cx.ntiles; t += gridDim.x) {
+        for (int s = gw; s < cx.nstrips; s += TW) {
             int c, row0, col0;
-            tile_of(t, c, row0, col0);
+            strip_of(s, c, row0, col0);
             const long long cbase = (long long)c * cx.HW;
-            load_w(b, c, true);
-            load_tile(sA, pitch, cx.TH + 2 * r, 32 + 2 * r, H, W, cbase, row0 - r, col0 - r,
-                      [=](long long g) { return __ldcg(v + g); });
-            load_tile(sB, pitch, cx.TH + 2 * r, 32 + 2 * r, H, W, cbase, row0 - r, col0 - r,
-                      [=](long long g) { return __ldcg(x + g); });
-            __syncthreads();
+            stage_halo(hA, v, cbase, row0, col0);
+            stage_halo(hB, x, cbase, row0, col0);
+            cp_async_wait_all();
+            __syncwarp();
             T au[MR], av[MR];
-#pragma unroll
-            for (int m = 0; m < MR; ++m) { au[m] = T(0); av[m] = T(0); }
-            const int li0 = warp * MR;
-            corr_strip<T, MR>(sA, pitch, sw, K, li0, lane, au);
-            corr_strip<T, MR>(sB, pitch, sw, K, li0, lane, av);
+            corr(hA, true, c, au);
+            corr(hB, true, c, av);
             const int gj = col0 + lane;
 #pragma unroll
             for (int m = 0; m < MR; ++m) {
-                const int gi = row0 + li0 + m;
+                const int gi = row0 + m;
                 if (gi < H && gj < W) {
                     const long long g = cbase + (long long)gi * W + gj;
                     U[g] = au[m];
                     V[g] = av[m] - __ldg(y + g);
                 }
             }
-            __syncthreads();
+            __syncwarp();
         }
         if (!sync()) return 0.0;
-        // phase K2: per-CTA lag sums over its tiles
-        double *zp = cx.zpart + (long long)blockIdx.x * CKK;
-        for (int e = tid; e < CKK; e += NT) zp[e] = 0.0;
-        for (int t = blockIdx.x; t < cx.ntiles; t += gridDim.x) {
+        // phase K2: lag sums of this warp's strips.  A lane owns lag row p and
+        // QB consecutive lag columns q0..q0+QB-1; along each strip row the x and
+        // v windows slide through registers (one new shared load each per column).
+        const int nqb = (K + QB - 1) / QB, units = K * nqb;
+        for (int s = gw; s < cx.nstrips; s += TW) {
             int c, row0, col0;
-            tile_of(t, c, row0, col0);
+            strip_of(s, c, row0, col0);
             const long long cbase = (long long)c * cx.HW;
-            load_tile(sA, pitch, cx.TH + 2 * r, 32 + 2 * r, H, W, cbase, row0 - r, col0 - r,
-                      [=](long long g) { return __ldcg(x + g); });
-            load_tile(sB, pitch, cx.TH + 2 * r, 32 + 2 * r, H, W, cbase, row0 - r, col0 - r,
-                      [=](long long g) { return __ldcg(v + g); });
-            for (int e = tid; e < cx.TH * 32; e += NT) {
-                const int li = e >> 5, lj = e & 31;
-                const int gi = row0 + li, gj = col0 + lj;
+            stage_halo(hA, x, cbase, row0, col0);
+            stage_halo(hB, v, cbase, row0, col0);
+            const int gj = col0 + lane;
+            for (int m = 0; m < MR; ++m) {
+                const int gi = row0 + m;
                 const bool in = gi < H && gj < W;
                 const long long g = cbase + (long long)gi * W + gj;
-                sU[e] = in ? __ldcg(U + g) : T(0);
-                sV[e] = in ? __ldcg(V + g) : T(0);
+                t1[m * 32 + lane] = in ? __ldcg(U + g) : T(0);
+                t2[m * 32 + lane] = in ? __ldcg(V + g) : T(0);
             }
-            __syncthreads();
-            for (int l = tid; l < KK; l += NT) {
-                const int p = l / K, q = l - p * K;
-                const int off = (2 * r - p) * pitch + (2 * r - q);
-                double acc = 0.0;
-                for (int li = 0; li < cx.TH; ++li) {
-                    T s = T(0);
-                    const T *xa = sA + off + li * pitch, *va = sB + off + li * pitch;
-                    const T *ur = sU + li * 32, *vr = sV + li * 32;
-#pragma unroll 8
-                    for (int lj = 0; lj < 32; ++lj) s = fma(xa[lj], ur[lj], fma(va[lj], vr[lj], s));
-                    acc += (double)s;
+            cp_async_wait_all();
+            __syncwarp();
+            for (int u = lane; u < units; u += 32) {
+                const int p = u / nqb, q0 = (u - p * nqb) * QB;
+                double acc[QB];
+#pragma unroll
+                for (int k = 0; k < QB; ++k) acc[k] = 0.0;
+                for (int m = 0; m < MR; ++m) {
+                    const T *rx = hA + (m + 2 * r - p) * cx.PA;
+                    const T *rv = hB + (m + 2 * r - p) * cx.PA;
+                    const T *ur = t1 + m * 32, *vr = t2 + m * 32;
+                    const int c0 = 2 * r - q0;       // column of lag q0 at j = 0
+                    T wx[QB], wv[QB], af[QB];
+#pragma unroll
+                    for (int k = 0; k < QB; ++k) af[k] = T(0);
+#pragma unroll
+                    for (int k = 1; k < QB; ++k) {
+                        const int col = c0 - k >= 0 ? c0 - k : 0;   // only unused lags clamp
+                        wx[(QB - k) % QB] = rx[col];
+                        wv[(QB - k) % QB] = rv[col];
+                    }
+                    for (int j0 = 0; j0 < 32; j0 += QB) {
+#pragma unroll
+                        for (int jj = 0; jj < QB; ++jj) {
+                            const int j = j0 + jj;
+                            wx[jj] = rx[c0 + j];
+                            wv[jj] = rv[c0 + j];
+                            const T uu = ur[j], vv = vr[j];
+#pragma unroll
+                            for (int k = 0; k < QB; ++k)
+                                af[k] = fma(wx[(jj - k + QB) % QB], uu, fma(wv[(jj - k + QB) % QB], vv, af[k]));
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < QB; ++k) acc[k] += (double)af[k];
                 }
-                zp[c * KK + l] += acc;
+#pragma unroll
+                for (int k = 0; k < QB; ++k)
+                    if (q0 + k < K) zp[c * KK + p * K + q0 + k] += acc[k];
             }
-            __syncthreads();
+            __syncwarp();
         }
         if (!sync()) return 0.0;
-        // phase K3: fixed-order sum over CTAs, sign, Sobolev term
-        const long long gs = gstride();
-        for (long long e = gstart(); e < CKK; e += gs) {
+        // phase K3: fixed-order sum over warps, sign, Sobolev term
+        for (long long e = gstart(); e < CKK; e += gstride()) {
             double s = 0.0;
-            for (int cta = 0; cta < (int)gridDim.x; ++cta) s += __ldcg(cx.zpart + (long long)cta * CKK + e);
+            for (int w = 0; w < TW; ++w) s += __ldcg(cx.zpart + (long long)w * CKK + e);
             double zz = negate ? -s : s;
             if (add_r) zz += grad_sobolev_elem(b, (int)e);
             zout[e] = (T)zz;
@@ -499,11 +684,13 @@ struct Eng {
         passes += 4;   // B v, B x and the two lag correlations
         if (!sync()) return 0.0;
         double s = 0.0;
-        for (int e = tid; e < CKK; e += NT) { const double zv = (double)__ldcg(zout + e); s += zv * zv; }
+        for (int e = tid; e < CKK; e += blockDim.x) { const double zv = (double)__ldcg(zout + e); s += zv * zv; }
         return block_sum(s, red);
     }
 
     // ------------------------------------------------------------ MAID
+    // One upper iteration of Algorithm 2; every CTA runs the same control flow
+    // on identical reduction results.
     __device__ void maid(const Job<T> &jb)
     {
         MaidIn st = jb.maid;
@@ -534,7 +721,7 @@ struct Eng {
             bool done = false;
             for (int i = 0; i < j; ++i) {
                 ++trials;
-                // b' = b - step z (every CTA writes the same values to its share)
+                // b' = b - step z
                 for (long long e = gstart(); e < CKK; e += gstride())
                     cx.BT[e] = (T)((double)__ldcg(b + e) - st.step * (double)__ldcg(cx.ZK + e));
                 if (!sync()) break;
@@ -545,6 +732,7 @@ struct Eng {
                 double l1 = 0.0, gx1 = 0.0;
                 upper_loss(cx.BT, cx.XT, l1, gx1, passes);
                 if (!alive) break;
+                // psi of Eq. 3.4 with eps_bar = eps_k
                 const double eb = st.eps;
                 psi = l1 + gx1 * eb + 0.5 * st.L_gx * eb * eb - l0 + gx0 * eb + st.lambda * st.step * zz;
                 if (psi <= 0.0) {
@@ -580,22 +768,23 @@ struct Eng {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(NT) adp_kernel(const __grid_constant__ Ctx<T> cx,
-                                                  const __grid_constant__ Job<T> jb)
+__global__ void __launch_bounds__(MAXNW * 32, 1) adp_kernel(const __grid_constant__ Ctx<T> cx,
+                                                         const __grid_constant__ Job<T> jb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[NW];
+    __shared__ double red[MAXNW];
     __shared__ double bcast;
     __shared__ double tau[MAXC];
+    __shared__ double gbuf[GT_MAX];
     __shared__ int sflag;
-    Eng<T> e(cx, smem_raw, red, &bcast, tau, &sflag);
+    Eng<T> e(cx, smem_raw, red, &bcast, tau, gbuf, &sflag);
     const bool lead = threadIdx.x == 0 && blockIdx.x == 0;
     long long passes = 0;
     switch (jb.mode) {
     case M_APPLY_B: e.apply(jb.b, jb.x, jb.xo, false); break;
     case M_APPLY_BT: e.apply(jb.b, jb.x, jb.xo, true); break;
     case M_GRAD_LOWER: e.grad_lower(jb.b, jb.x, jb.xo); break;
-    case M_HESS_VEC: e.hess_vec(jb.b, jb.x, jb.v, jb.xo); break;
+    case M_HESS_VEC: e.load_weights(jb.b); e.hess_vec(jb.x, jb.v, jb.xo); break;
     case M_LOWER_SOLVE: {
         double gn = 0.0;
         const int it = e.lower_solve(jb.b, jb.x, jb.xo, jb.eps, jb.max_iters, gn, passes);
@@ -636,6 +825,7 @@ __global__ void __launch_bounds__(NT) adp_kernel(const __grid_constant__ Ctx<T> 
     case M_MAID: e.maid(jb); break;
     default: break;
     }
+    if (lead) cx.out->barriers = (int)e.epoch;
 }
 
 } // namespace adp
