@@ -217,7 +217,11 @@ adp_status adp_problem_create(const adp_params *prm, const void *y, const void *
     p->nw = nw;
     p->smem = (size_t)total * p->esize;
     const void *kfn = q.prec == ADP_F32 ? kernel_f32() : kernel_f64();
-    CKC(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem));
+    // opt in to the device's whole dynamic shared memory (less the static part)
+    // rather than this problem's size: the attribute is shared by every problem
+    // on the device, and a smaller value set for a later problem with a smaller
+    // K would make launches of an earlier, larger problem fail
+    CKC(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem - 5 * 1024));
     int occ = 0;
     CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, 32 * nw, p->smem));
     if (occ < 1) {

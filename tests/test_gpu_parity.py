@@ -260,3 +260,17 @@ def test_invalid_arguments_are_rejected():
     pr = adp.Problem(adp.Params(1, 16, 16, 3), y, a)
     with pytest.raises(TypeError):
         pr.apply_B(a.double(), y)
+
+
+def test_problems_with_different_kernel_sizes_coexist():
+    # the kernel's shared-memory opt-in is shared by all problems on a device:
+    # creating a problem with a small K after one with a large K must not break
+    # the large one's launches
+    big = Pair(inst_for(1, 40, 40, 31), prec=adp.ADP_F32)
+    small = Pair(inst_for(1, 40, 40, 3), prec=adp.ADP_F32)
+    rng = np.random.default_rng(0)
+    for pr in (big, small, big):
+        x = pr.rounded(rng.uniform(size=(1, 40, 40)))
+        b = pr.rounded(pr.inst.b_true)
+        out = pr.prob.apply_B(pr.t(b), pr.t(x))
+        assert rel(pr.n(out), pr.P.conv(b, x)) <= OP_TOL[adp.ADP_F32]
