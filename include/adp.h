@@ -160,6 +160,34 @@ int adp_warps_per_cta(adp_problem *p);
  * events recorded on the problem's stream around the launch. */
 double adp_last_kernel_ms(adp_problem *p);
 
+/* Lower-level solve that allocates nothing.  There is no counterpart in the
+ * paper: this is an engineering variant of adp_lower_solve for callers that
+ * cannot allocate device memory when they need a solve -- cudaMalloc/cudaFree
+ * synchronise the device (unacceptable inside a latency-critical or real-time
+ * loop), and callers that give all device memory to their own pool or run
+ * under a memory budget fixed at start-up must not have a library allocate.
+ *
+ * Same computation as adp_lower_solve (FISTA on h(., b) from the warm start in
+ * x, stopped at ||grad_x h(y_k, b)|| <= eps or after max_iters updates; x
+ * receives y_k; ADP_ENOCONV at the cap), but without an adp_problem: y
+ * (C x H x W), b (C x K x K) and x are the caller's device pointers, `stream`
+ * a cudaStream_t, and the workspace is one fixed array in the library's
+ * device memory, ADP_NOALLOC_SCRATCH_BYTES in size, which every GPU that
+ * loads the library holds until the process exits.  Images are limited to
+ * C*H*W*element size <= ADP_NOALLOC_MAX_IMAGE_BYTES (e.g. 3 x 512 x 512 in
+ * FP32); larger ones are rejected with ADP_EINVAL.  The first call on a device
+ * looks up the array's device address and sets kernel attributes for that
+ * device (once per device, with it current); make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents (each call clears what must start at zero), so calls whose GPU work
+ * overlaps -- on different streams, or from different threads -- race and
+ * must be serialised by the caller.  Calls no cudaMalloc, cudaFree or other
+ * allocating routine. */
+#define ADP_NOALLOC_MAX_IMAGE_BYTES 3276800
+#define ADP_NOALLOC_SCRATCH_BYTES (512 + 8 * 512 * 8 + 5 * ADP_NOALLOC_MAX_IMAGE_BYTES)
+adp_status adp_lower_solve_noalloc(const adp_params *params, const void *y, const void *b, void *x, double eps,
+                                   int max_iters, void *stream, int *iters, double *gradnorm);
+
 /* Tracing (diagnostics).  With cap > 0, later calls on p record, for the first
  * cap grid barriers of each launch, the device global timer (ns) when CTA 0
  * arrived at and left the barrier; cap = 0 turns tracing off.  Allocates (and

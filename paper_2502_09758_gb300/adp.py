@@ -29,7 +29,7 @@ EXPORTS = ("adp_problem_create", "adp_problem_destroy", "adp_apply_B", "adp_appl
            "adp_grad_lower", "adp_hess_vec", "adp_lower_solve", "adp_upper_loss", "adp_hypergrad",
            "adp_cross_t", "adp_maid_init", "adp_maid_step", "adp_conv_passes_last",
            "adp_grid_size", "adp_warps_per_cta", "adp_last_kernel_ms", "adp_trace_enable",
-           "adp_trace_read", "adp_last_error", "adp_status_string")
+           "adp_trace_read", "adp_lower_solve_noalloc", "adp_last_error", "adp_status_string")
 
 
 class AdpError(RuntimeError):
@@ -90,6 +90,7 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
             "adp_last_kernel_ms": (ct.c_double, [P]),
             "adp_trace_enable": (i, [P, i]),
             "adp_trace_read": (i, [P, ct.POINTER(ct.c_longlong), i]),
+            "adp_lower_solve_noalloc": (i, [ct.POINTER(adp_params), vp, vp, vp, d, i, vp, ip, dp]),
             "adp_last_error": (ct.c_char_p, []),
             "adp_status_string": (ct.c_char_p, [i]),
         }
@@ -308,6 +309,22 @@ def adp_maid_step(prob: Problem, state, b, x, q):
 
 def adp_maid_init(prob: Problem, **overrides):
     return prob.maid_init(**overrides)
+
+
+def adp_lower_solve_noalloc(params: Params, y, b, x, eps, max_iters=300, stream=None):
+    """adp_lower_solve without any device allocation (workspace in a fixed
+    library array): for callers that cannot allocate device memory where they
+    need the solve.  In place on x; returns (updates, ||grad_x h||, capped)."""
+    lib = load_library()
+    img, ker = (params.C, params.H, params.W), (params.C, params.K, params.K)
+    s = stream if stream is not None else torch.cuda.current_stream(x.device)
+    it, gn = ct.c_int(), ct.c_double()
+    cp = params.c()
+    st = _check(lib.adp_lower_solve_noalloc(ct.byref(cp), _ptr(y, img, params.dtype, "y"),
+                                            _ptr(b, ker, params.dtype, "b"), _ptr(x, img, params.dtype, "x"),
+                                            float(eps), int(max_iters), ct.c_void_p(s.cuda_stream),
+                                            ct.byref(it), ct.byref(gn)), ok=(ADP_OK, ADP_ENOCONV))
+    return it.value, gn.value, st == ADP_ENOCONV
 
 
 # ----------------------------------------------------------------- autograd

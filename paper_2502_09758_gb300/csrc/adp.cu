@@ -29,6 +29,11 @@ const void *kernel_f64();
 
 static thread_local char g_err[512];
 
+namespace adp {
+// lets the other translation units of the library report through adp_last_error
+void record_error(const char *msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+} // namespace adp
+
 static adp_status set_err(adp_status s, const char *fmt, const char *a = "", long long v = 0)
 {
     snprintf(g_err, sizeof g_err, fmt, a, v);
