@@ -1,15 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the ADP-beta / MAID hot path on GB300.
 
-One step = one MAID upper iteration (Algorithm 2) on the 256 x 256 RGB,
-15 x 15 motion-blur workload: the lower-level FISTA solves, the upper loss,
-the CG solve of the IFT hypergradient, the kernel-gradient correlation and the
-backtracking trials with their re-solves, all inside one cooperative launch
-of libadp.  Steps continue one MAID trajectory (paper defaults, Sec. 4.1);
-W warm-up steps run first.
+Workload: 256 x 256 RGB, 15 x 15 motion blur (length 11 at 30 deg; b_0 = the
+same blur at 20 deg), noise 0.02, Huber-TV lower level (alpha 1e-2, gamma 1e-2),
+Sobolev upper level (beta 0.3), FP32 operators with FP64 reductions.
+
+One step = one complete MAID run (Algorithm 2) from b_0 and x_0 = y until the
+stop rule of Sec. 4.2 fires (eps <= eps_stop) or MAX_UPPER upper iterations
+have run: the lower-level FISTA solves, the upper losses, the CG solves of the
+IFT hypergradient, the kernel-gradient correlations and the backtracking
+trials.  Each upper iteration is one cooperative launch of libadp
+(adp_maid_step); the host only reads the scalars at its end.
 
 value: Mvalue*iter/s = (C*H*W values) x (FISTA + CG iterations executed in
-the timed steps) / device time of those steps, summed over ranks (replicas).
+the timed runs) / device time of those runs, summed over ranks (replicas).
+Beside it: the time to tolerance per run, and the same runs driven from the
+host with one launch per solve ("plain GPU MAID").
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -36,6 +42,8 @@ SM_COUNT, FP32_LANES = 152, 128
 # eps_0 in {1e-2, 1e-3, 1e-4} x alpha_0 in {1e-1, 1e-5, 1e-6, 1e-7} (every
 # step accepted, least time), as the paper picks alpha and beta by grid search
 EPS0, STEP0 = 1e-4, 1e-6
+EPS_STOP = 5e-5        # stop rule (Sec. 4.2): near the FP32 floor of ||grad_x h|| at this size
+MAX_UPPER = 40         # cap on upper iterations per run
 
 
 def peaks():
@@ -141,6 +149,73 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def maid_run(prob, a, y, b_h=None, x_h=None):
+    """One MAID run on the device driver; returns (device ms, fused iters,
+    conv passes, upper iterations, accepted, b, x, state)."""
+    import torch
+    b = a.clone() if b_h is None else b_h
+    x = y.clone() if x_h is None else x_h
+    q = torch.zeros_like(x)
+    st = prob.maid_init(eps=EPS0, delta=EPS0, step=STEP0, eps_stop=EPS_STOP)
+    ms, iters, passes, ups, acc = 0.0, 0, 0, 0, 0
+    for _ in range(MAX_UPPER):
+        ok = prob.maid_step(st, b, x, q)
+        ms += prob.last_kernel_ms()
+        iters += st.ll_iters + st.cg_iters
+        passes += prob.conv_passes_last()
+        ups += 1
+        acc += int(ok)
+        if st.stopped or not ok:
+            break
+    return ms, iters, passes, ups, acc, b, x, st
+
+
+def plain_maid_run(prob, a, y):
+    """The same Algorithm 2 driven from the host: one launch per lower-level
+    solve, upper loss and hypergradient, scalars read back after each (the
+    plain GPU port).  Returns (wall ms, upper iterations, b, x)."""
+    import torch
+    b, x = a.clone(), y.clone()
+    s = prob.maid_init(eps=EPS0, delta=EPS0, step=STEP0, eps_stop=EPS_STOP)
+    eps, delta, step = s.eps, s.delta, s.step
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ups = 0
+    stopped = eps <= EPS_STOP
+    while ups < MAX_UPPER and not stopped:
+        ups += 1
+        accepted = False
+        j = s.max_bt
+        for _ in range(s.max_rounds):
+            prob.lower_solve(b, x, eps, s.ll_max_iters)
+            l0, gx0 = prob.upper_loss(b, x)
+            z, _, _, _, _ = prob.hypergrad(b, x, delta, max_iters=s.cg_max_iters)
+            zz = float((z.double() ** 2).sum())
+            for _ in range(j):
+                bt = (b.double() - step * z.double()).float()
+                xt = x.clone()
+                prob.lower_solve(bt, xt, eps, s.ll_max_iters)
+                l1, gx1 = prob.upper_loss(bt, xt)
+                psi = l1 + gx1 * eps + 0.5 * s.L_gx * eps * eps - l0 + gx0 * eps + s.lam * step * zz
+                if psi <= 0.0:
+                    b, x = bt, xt
+                    eps, delta, step = eps * s.nu_up, delta * s.nu_up, step * s.rho_up
+                    accepted = True
+                    break
+                step *= s.rho_down
+            if accepted:
+                break
+            eps, delta = eps * s.nu_down, delta * s.nu_down
+            j += 1
+            if eps <= EPS_STOP:
+                stopped = True
+                break
+        if not accepted:
+            break
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) * 1e3, ups, b, x
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -163,11 +238,8 @@ def run_ours(args):
     y = torch.tensor(inst.y, dtype=torch.float32, device=dev)
     a = torch.tensor(inst.a, dtype=torch.float32, device=dev)
     prob = adp.Problem(adp.Params(C, H, W, K, alpha=1e-2, reg_param=1e-2, beta=0.3), y, a)
-    b, x = a.clone(), y.clone()
-    q = torch.zeros_like(x)
-    st = prob.maid_init(eps=EPS0, delta=EPS0, step=STEP0)
     for _ in range(args.warmup):
-        prob.maid_step(st, b, x, q)
+        maid_run(prob, a, y)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -177,24 +249,25 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clk.start()
-    step_ms, kern_ms, iters, passes, accepted = [], [], 0, 0, 0
+    run_ms, kern_ms, iters, passes, ups, accepted = [], 0.0, 0, 0, 0, 0
     for _ in range(args.steps):
-        flush.zero_()                       # L2 flush between timed steps (not timed)
+        flush.zero_()                       # L2 flush between timed runs (not timed)
         ev0.record()
-        ok = prob.maid_step(st, b, x, q)
+        kms, it, ps, u, acc, b, x, st = maid_run(prob, a, y)
         ev1.record()
         ev1.synchronize()
-        step_ms.append(ev0.elapsed_time(ev1))
-        kern_ms.append(prob.last_kernel_ms())
-        iters += st.ll_iters + st.cg_iters
-        passes += prob.conv_passes_last()
-        accepted += int(ok)
+        run_ms.append(ev0.elapsed_time(ev1))
+        kern_ms += kms
+        iters += it
+        passes += ps
+        ups += u
+        accepted += acc
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = clk.stop()
 
-    tot_ms = sum(step_ms)
+    tot_ms = sum(run_ms)
     units = N * iters
     if world > 1:
         t = torch.tensor([tot_ms, units], dtype=torch.float64, device=dev)
@@ -206,22 +279,35 @@ def run_ours(args):
         tot_ms_max, units_all = tot_ms, float(units)
     value = units_all / (tot_ms_max / 1e3) / 1e6
 
-    # end to end through the public API with host buffers: H2D of the step's
-    # inputs (b, x~ warm start) from pinned memory, the call, D2H of b, x~, loss
-    b_h = b.cpu().pin_memory()
-    x_h = x.cpu().pin_memory()
+    xr, br = x.double().cpu().numpy(), b.double().cpu().numpy()
+    psnr_x = 10 * np.log10(1.0 / np.mean((xr - inst.x_true) ** 2))
+    psnr_b = 10 * np.log10(float(np.max(inst.b_true)) ** 2 / np.mean((br - inst.b_true) ** 2))
+
+    # the plain host-driven GPU MAID on the same runs (two runs, the first warm)
+    plain_maid_run(prob, a, y)
+    pms, pups, pb, px = plain_maid_run(prob, a, y)
+    pxr = px.double().cpu().numpy()
+    plain_psnr = 10 * np.log10(1.0 / np.mean((pxr - inst.x_true) ** 2))
+
+    # end to end through the public API with host buffers: per run, H2D of the
+    # inputs (b_0, x_0) from pinned memory, the run, D2H of b, x~ and the loss
+    b0_h = a.cpu().pin_memory()
+    x0_h = y.cpu().pin_memory()
+    bo_h = torch.empty_like(b0_h).pin_memory()
+    xo_h = torch.empty_like(x0_h).pin_memory()
+    bd, xd = torch.empty_like(a), torch.empty_like(y)
     e2e_ms, e2e_units = 0.0, 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        b.copy_(b_h, non_blocking=True)
-        x.copy_(x_h, non_blocking=True)
-        prob.maid_step(st, b, x, q)
-        b_h.copy_(b, non_blocking=True)
-        x_h.copy_(x, non_blocking=True)
+        bd.copy_(b0_h, non_blocking=True)
+        xd.copy_(x0_h, non_blocking=True)
+        _, it, _, _, _, b2, x2, st2 = maid_run(prob, a, y, bd, xd)
+        bo_h.copy_(b2, non_blocking=True)
+        xo_h.copy_(x2, non_blocking=True)
         torch.cuda.synchronize()
-        _ = float(st.loss)
+        _ = float(st2.loss)
         e2e_ms += (time.perf_counter() - t0) * 1e3
-        e2e_units += N * (st.ll_iters + st.cg_iters)
+        e2e_units += N * it
     esz = 4
     h2d = (C * K * K + N) * esz
     d2h = (C * K * K + N) * esz + 8
@@ -230,25 +316,30 @@ def run_ours(args):
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     peak_tf = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
     flops = passes * 2.0 * K * K * N
-    achieved = flops / (sum(kern_ms) / 1e3) / 1e12
+    achieved = flops / (kern_ms / 1e3) / 1e12
+    traffic = committed_traffic(ups)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "C": C, "H": H, "W": W, "K": K, "alpha": 1e-2, "huber": 1e-2,
-                   "beta": 0.3, "maid_eps0": EPS0, "maid_step0": STEP0,
-                   "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": f"replicas x{world}"},
-        "maid": {"upper_iters_timed": args.steps, "accepted": accepted,
-                 "fused_iters_per_step": iters / args.steps, "eps_end": st.eps,
-                 "grid_ctas": prob.grid_size()},
+                   "beta": 0.3, "maid_eps0": EPS0, "maid_step0": STEP0, "eps_stop": EPS_STOP,
+                   "max_upper": MAX_UPPER, "step": "one MAID run to the stop rule",
+                   "l2": "flushed between timed runs (256 MB write)", "parallelism": f"replicas x{world}"},
+        "maid": {"time_to_tolerance_s": tot_ms_max / args.steps / 1e3,
+                 "plain_gpu_maid_s": pms / 1e3, "speedup_vs_plain": pms / (tot_ms_max / args.steps),
+                 "upper_iters_per_run": ups / args.steps, "accepted_per_run": accepted / args.steps,
+                 "fused_iters_per_run": iters / args.steps, "eps_end": st.eps, "stopped": bool(st.stopped),
+                 "final_psnr_x_db": psnr_x, "final_psnr_b_db": psnr_b, "plain_final_psnr_x_db": plain_psnr,
+                 "grid_ctas": prob.grid_size(), "warps_per_cta": prob.warps_per_cta()},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tf, "traffic": None,
+                     "frac": achieved / peak_tf, "traffic": traffic,
                      "kernel": "adp_kernel<float> (persistent MAID step)",
-                     "peak_basis": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"},
+                     "peak_basis": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
+                     "flops_basis": "2 K^2 C H W per convolution pass, passes counted on the device"},
         "e2e": {"value": e2e_units / (e2e_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps,
+        "gpu_launches": ups,
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -260,6 +351,24 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def committed_traffic(upper_iters):
+    """DRAM bytes per launch of the MAID kernel from the committed ncu summary,
+    or None when the kernel sources changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "maid_step_rgb256_k15_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2502_09758_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    if rec.get("sources_sha256") != h.hexdigest():
+        return None
+    return rec.get("dram_bytes_per_launch")
 
 
 def main():

@@ -127,15 +127,19 @@ typedef struct {
     double rho_up, rho_down;          /* 1.1, 0.5                                         */
     double nu_up, nu_down;            /* 1.25, 0.5                                        */
     double L_gx;                      /* Lipschitz constant of grad g; set by adp_maid_init */
+    double eps_stop;                  /* stop rule of Sec. 4.2: the upper iterations end once
+                                         eps <= eps_stop (0 turns the rule off)            */
     int max_bt, max_rounds;           /* first inner-loop length (5), outer rounds (20)    */
     int ll_max_iters, cg_max_iters;   /* 300 (Sec. 4.1), 1000                             */
     int k;                            /* accepted upper iterations so far                  */
     /* report of the last adp_maid_step */
     int accepted, rounds, trials, ll_iters, cg_iters, ll_capped, cg_capped;
+    int stopped;                      /* the stop rule fired (b, x unchanged)              */
     double loss, gradx_norm, znorm, psi;
 } adp_maid_state;
 
-/* Fills `s` with the paper's defaults and L_gx = 2 max_c ||a_c||_1^2. */
+/* Fills `s` with the paper's defaults, eps_stop = 0 (rule off) and
+ * L_gx = 2 max_c ||a_c||_1^2. */
 adp_status adp_maid_init(adp_problem *p, adp_maid_state *s);
 
 /* One upper iteration of Algorithm 2 (MAID), entirely on the device in one
@@ -145,7 +149,10 @@ adp_status adp_maid_init(adp_problem *p, adp_maid_state *s);
  * failed round eps and delta shrink and the gradient is recomputed.
  * b (C x K x K) and x (C x H x W, x~(b_k) in, x~(b_{k+1}) out) are in/out; q
  * (C x H x W) receives the last CG solution.  Returns ADP_ELSFAIL when all
- * rounds failed (b, x unchanged; s reports the shrunk eps, delta, step). */
+ * rounds failed (b, x unchanged; s reports the shrunk eps, delta, step).  The
+ * stop rule (eps <= eps_stop) is checked on entry and after every decrease of
+ * eps; when it fires the call returns ADP_OK with s->stopped = 1,
+ * s->accepted = 0 and b, x unchanged. */
 adp_status adp_maid_step(adp_problem *p, adp_maid_state *s, void *b, void *x, void *q);
 
 /* Diagnostics of the last call on p: number of full-image convolution passes

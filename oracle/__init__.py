@@ -35,11 +35,12 @@ class MaidState(ct.Structure):
     _fields_ = [("eps", ct.c_double), ("delta", ct.c_double), ("step", ct.c_double),
                 ("lam", ct.c_double), ("rho_up", ct.c_double), ("rho_down", ct.c_double),
                 ("nu_up", ct.c_double), ("nu_down", ct.c_double), ("L_gx", ct.c_double),
+                ("eps_stop", ct.c_double),
                 ("max_bt", ct.c_int), ("max_rounds", ct.c_int), ("ll_max_iters", ct.c_int),
                 ("cg_max_iters", ct.c_int), ("k", ct.c_int),
                 ("accepted", ct.c_int), ("rounds", ct.c_int), ("trials", ct.c_int),
                 ("ll_iters", ct.c_int), ("cg_iters", ct.c_int), ("ll_capped", ct.c_int),
-                ("cg_capped", ct.c_int),
+                ("cg_capped", ct.c_int), ("stopped", ct.c_int),
                 ("loss", ct.c_double), ("gradx_norm", ct.c_double), ("znorm", ct.c_double),
                 ("psi", ct.c_double)]
 

@@ -52,10 +52,11 @@ typedef struct {
     double eps, delta, step;
     /* hyper-parameters of Algorithm 2 and Eq. 3.4 */
     double lambda, rho_up, rho_down, nu_up, nu_down, L_gx;
+    double eps_stop;       /* stop rule of Sec. 4.2: stop once eps <= eps_stop (0: off) */
     int max_bt, max_rounds, ll_max_iters, cg_max_iters;
     int k;                 /* upper iterations accepted so far */
     /* report of the last call */
-    int accepted, rounds, trials, ll_iters, cg_iters, ll_capped, cg_capped;
+    int accepted, rounds, trials, ll_iters, cg_iters, ll_capped, cg_capped, stopped;
     double loss, gradx_norm, znorm, psi;
 } orc_maid;
 
@@ -488,7 +489,10 @@ void orc_maid_init(orc_maid *s)
  * decrease psi of Eq. 3.4.  x holds x~(b_k) on entry (warm start) and
  * x~(b_{k+1}) on exit; q receives the last CG solution.  Returns 1 when a step
  * was accepted, 0 when the backtracking rounds ran out (b unchanged, eps/delta
- * and the step already shrunk). */
+ * and the step already shrunk).  The stop rule of Sec. 4.2 (the upper
+ * iterations end once the accuracy eps reaches eps_stop) is checked on entry
+ * and after every decrease of eps; when it fires the call returns 0 with
+ * stopped = 1 and b unchanged. */
 int orc_maid_step(const orc_prob *p, orc_maid *s, const double *a, const double *y,
                   double *b, double *x, double *q)
 {
@@ -498,7 +502,12 @@ int orc_maid_step(const orc_prob *p, orc_maid *s, const double *a, const double 
     double gn, res;
     int capped, j = s->max_bt;
     s->accepted = 0; s->rounds = 0; s->trials = 0; s->ll_iters = 0; s->cg_iters = 0;
-    s->ll_capped = 0; s->cg_capped = 0;
+    s->ll_capped = 0; s->cg_capped = 0; s->stopped = 0;
+    if (s->eps_stop > 0.0 && s->eps <= s->eps_stop) {
+        s->stopped = 1;
+        free(z); free(bt); free(xt);
+        return 0;
+    }
     for (int round = 0; round < s->max_rounds; ++round, ++j) {
         s->rounds = round + 1;
         /* InexactGradient(b_k, eps_k, delta_k) */
@@ -538,6 +547,7 @@ int orc_maid_step(const orc_prob *p, orc_maid *s, const double *a, const double 
         }
         s->loss = l0; s->gradx_norm = gx0;
         s->eps *= s->nu_down; s->delta *= s->nu_down;
+        if (s->eps_stop > 0.0 && s->eps <= s->eps_stop) { s->stopped = 1; break; }
     }
     free(z); free(bt); free(xt);
     return 0;

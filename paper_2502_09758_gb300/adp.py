@@ -49,11 +49,12 @@ class adp_maid_state(ct.Structure):
     _fields_ = [("eps", ct.c_double), ("delta", ct.c_double), ("step", ct.c_double),
                 ("lam", ct.c_double), ("rho_up", ct.c_double), ("rho_down", ct.c_double),
                 ("nu_up", ct.c_double), ("nu_down", ct.c_double), ("L_gx", ct.c_double),
+                ("eps_stop", ct.c_double),
                 ("max_bt", ct.c_int), ("max_rounds", ct.c_int), ("ll_max_iters", ct.c_int),
                 ("cg_max_iters", ct.c_int), ("k", ct.c_int),
                 ("accepted", ct.c_int), ("rounds", ct.c_int), ("trials", ct.c_int),
                 ("ll_iters", ct.c_int), ("cg_iters", ct.c_int), ("ll_capped", ct.c_int),
-                ("cg_capped", ct.c_int),
+                ("cg_capped", ct.c_int), ("stopped", ct.c_int),
                 ("loss", ct.c_double), ("gradx_norm", ct.c_double), ("znorm", ct.c_double),
                 ("psi", ct.c_double)]
 
@@ -261,10 +262,11 @@ class Problem:
         return s
 
     def maid_step(self, state: adp_maid_state, b, x, q):
-        """One upper iteration of Algorithm 2 in place on b, x, q; returns accepted."""
+        """One upper iteration of Algorithm 2 in place on b, x, q; returns
+        accepted (False also when the stop rule fired: see state.stopped)."""
         st = _check(self.lib.adp_maid_step(self.handle, ct.byref(state), self._k(b, "b"), self._i(x, "x"),
                                            self._i(q, "q")), ok=(ADP_OK, ADP_ELSFAIL))
-        return st == ADP_OK
+        return st == ADP_OK and bool(state.accepted)
 
     def conv_passes_last(self) -> int:
         return int(self.lib.adp_conv_passes_last(self.handle))

@@ -379,7 +379,7 @@ adp_status adp_maid_step(adp_problem *p, adp_maid_state *s, void *b, void *x, vo
     MaidIn mi;
     mi.eps = s->eps; mi.delta = s->delta; mi.step = s->step; mi.lambda = s->lambda;
     mi.rho_up = s->rho_up; mi.rho_down = s->rho_down; mi.nu_up = s->nu_up; mi.nu_down = s->nu_down;
-    mi.L_gx = s->L_gx; mi.max_bt = s->max_bt; mi.max_rounds = s->max_rounds;
+    mi.L_gx = s->L_gx; mi.eps_stop = s->eps_stop; mi.max_bt = s->max_bt; mi.max_rounds = s->max_rounds;
     mi.ll_max_iters = s->ll_max_iters; mi.cg_max_iters = s->cg_max_iters; mi.k = s->k;
     adp_status st = dispatch_job(p, M_MAID, nullptr, x, nullptr, nullptr, q, nullptr, b, 0, 0, 0, &mi);
     if (st != ADP_OK) return st;
@@ -388,7 +388,8 @@ adp_status adp_maid_step(adp_problem *p, adp_maid_state *s, void *b, void *x, vo
     s->accepted = o->accepted; s->rounds = o->rounds; s->trials = o->trials;
     s->ll_iters = o->ll_iters; s->cg_iters = o->cg_iters; s->ll_capped = o->ll_capped; s->cg_capped = o->cg_capped;
     s->loss = o->loss; s->gradx_norm = o->gradx_norm; s->znorm = o->znorm; s->psi = o->psi;
-    return o->accepted ? ADP_OK : ADP_ELSFAIL;
+    s->stopped = o->stopped;
+    return (o->accepted || o->stopped) ? ADP_OK : ADP_ELSFAIL;
 }
 
 long long adp_conv_passes_last(adp_problem *p) { return p ? p->hout->conv_passes : -1; }

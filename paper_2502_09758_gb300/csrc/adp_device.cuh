@@ -33,7 +33,7 @@ struct DevOut {
     int accepted, rounds, trials, ll_iters, ll_capped, cg_capped, k, pad;
     double eps, delta, step;
     long long conv_passes;       // number of full-image convolution passes executed
-    int barriers, pad2;          // grid barriers executed by CTA 0
+    int barriers, stopped;       // grid barriers executed by CTA 0; MAID stop rule fired
 };
 
 __host__ __device__ constexpr int round_up(int a, int m) { return (a + m - 1) / m * m; }
@@ -291,7 +291,7 @@ enum Mode : int {
 };
 
 struct MaidIn {
-    double eps, delta, step, lambda, rho_up, rho_down, nu_up, nu_down, L_gx;
+    double eps, delta, step, lambda, rho_up, rho_down, nu_up, nu_down, L_gx, eps_stop;
     int max_bt, max_rounds, ll_max_iters, cg_max_iters, k;
 };
 

@@ -698,9 +698,10 @@ struct Eng {
         const int CKK = cx.C * cx.K * cx.K;
         long long passes = 0;
         int ll_iters = 0, cg_iters = 0, ll_capped = 0, cg_capped = 0, trials = 0, rounds = 0, accepted = 0;
+        int stopped = st.eps_stop > 0.0 && st.eps <= st.eps_stop;   // stop rule of Sec. 4.2
         double loss = 0.0, gxn = 0.0, znorm = 0.0, psi = 0.0, gn = 0.0, res = 0.0;
         int j = st.max_bt;
-        for (int round = 0; round < st.max_rounds && alive; ++round, ++j) {
+        for (int round = 0; round < st.max_rounds && alive && !stopped; ++round, ++j) {
             rounds = round + 1;
             // InexactGradient(b_k, eps_k, delta_k)
             ll_iters += lower_solve(b, x, x, st.eps, st.ll_max_iters, gn, passes);
@@ -755,6 +756,7 @@ struct Eng {
             gxn = gx0;
             st.eps *= st.nu_down;
             st.delta *= st.nu_down;
+            if (st.eps_stop > 0.0 && st.eps <= st.eps_stop) stopped = 1;
         }
         if (tid == 0 && blockIdx.x == 0) {
             DevOut *o = cx.out;
@@ -762,7 +764,7 @@ struct Eng {
             o->ll_iters = ll_iters; o->cg_iters = cg_iters; o->ll_capped = ll_capped; o->cg_capped = cg_capped;
             o->k = st.k; o->eps = st.eps; o->delta = st.delta; o->step = st.step;
             o->loss = loss; o->gradx_norm = gxn; o->znorm = znorm; o->psi = psi;
-            o->conv_passes = passes;
+            o->conv_passes = passes; o->stopped = stopped;
         }
     }
 };

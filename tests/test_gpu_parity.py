@@ -274,3 +274,20 @@ def test_problems_with_different_kernel_sizes_coexist():
         b = pr.rounded(pr.inst.b_true)
         out = pr.prob.apply_B(pr.t(b), pr.t(x))
         assert rel(pr.n(out), pr.P.conv(b, x)) <= OP_TOL[adp.ADP_F32]
+
+
+def test_maid_stop_rule_matches_oracle():
+    inst = inst_for(1, 32, 32, 5)
+    pr = Pair(inst, prec=adp.ADP_F64, beta=0.3)
+    b, x = pr.t(pr.rounded(inst.a)), pr.t(pr.rounded(inst.y))
+    s = pr.prob.maid_init(step=1e12, max_rounds=10, max_bt=2, eps_stop=3e-3)
+    assert pr.prob.maid_step(s, b, x, torch.zeros_like(x)) is False
+    so = pr.P.maid_init(pr.a, step=1e12, max_rounds=10, max_bt=2, eps_stop=3e-3)
+    bo, xo = pr.rounded(inst.a), pr.rounded(inst.y)
+    pr.P.maid_step(so, pr.a, pr.y, bo, xo)
+    assert s.stopped == so.stopped == 1
+    assert (s.rounds, s.trials, s.eps, s.step) == (so.rounds, so.trials, so.eps, so.step)
+    # at entry: nothing runs
+    s2 = pr.prob.maid_init(eps=1e-3, delta=1e-3, eps_stop=1e-3)
+    assert pr.prob.maid_step(s2, b, x, torch.zeros_like(x)) is False
+    assert s2.stopped == 1 and s2.ll_iters == 0 and s2.rounds == 0

@@ -439,3 +439,21 @@ def test_maid_backtracking_exhaustion(orc):
     np.testing.assert_array_equal(b, inst.a)
     assert s.eps == pytest.approx(0.5e-2) and s.delta == pytest.approx(0.5e-2)
     assert s.step == pytest.approx(1e12 * 0.25) and s.trials == 2
+
+
+def test_maid_stop_rule_sec42(orc):
+    # Sec. 4.2: the upper iterations end when MAID's accuracy reaches the stop
+    # tolerance.  At entry: no work at all.  During backtracking: the step ends
+    # as soon as a failed round has shrunk eps to the tolerance.
+    inst = synth.small(C=1, H=8, W=8, K=3, seed=82)
+    P = orc.Problem(1, 8, 8, 3, alpha=0.05, reg=orc.REG_QUAD, beta=0.3)
+    s = P.maid_init(inst.a, eps=1e-3, delta=1e-3, eps_stop=1e-3)
+    b, x = inst.a.copy(), inst.y.copy()
+    acc, _ = P.maid_step(s, inst.a, inst.y, b, x)
+    assert not acc and s.stopped == 1 and s.ll_iters == 0 and s.rounds == 0
+    np.testing.assert_array_equal(x, inst.y)
+    s = P.maid_init(inst.a, step=1e12, max_rounds=10, max_bt=2, eps_stop=3e-3)
+    acc, _ = P.maid_step(s, inst.a, inst.y, b, x)
+    assert not acc and s.stopped == 1 and s.rounds == 2          # 1e-2 -> 5e-3 -> 2.5e-3
+    assert s.eps == pytest.approx(2.5e-3) and s.trials == 2 + 3
+    np.testing.assert_array_equal(b, inst.a)
