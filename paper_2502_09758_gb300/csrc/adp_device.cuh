@@ -102,19 +102,160 @@ __device__ __forceinline__ bool grid_sync(unsigned *count, unsigned epoch, int *
     return *s_flag != 0;
 }
 
+// ------------------------------------------------------------ scalars
+// Reductions and the iteration control of the FP32 path run in float-float
+// ("double-single") arithmetic: a value is an unevaluated sum hi + lo of two
+// floats, updated with the error-free transformations TwoSum and TwoProd
+// (Knuth; Dekker), which carry about 48 significant bits.  This keeps sums and
+// dot products near FP64 accuracy while using only the FP32 pipes: on GB300 an
+// FP64 instruction occupies the FP64 pipe for tens of cycles per warp.  The
+// FP64 path (T = double) uses plain doubles.  Every reduction runs in a fixed
+// order, so results are deterministic and identical in all CTAs.
+struct __align__(8) ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ ff fast_two_sum(float a, float b)   // |a| >= |b|
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    ff s = two_sum(a.hi, b.hi);
+    const ff t = two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ ff ff_add_f(ff a, float b)
+{
+    ff s = two_sum(a.hi, b);
+    s.lo = __fadd_rn(s.lo, a.lo);
+    return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ ff ff_div(ff a, ff b)
+{
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const ff r = ff_add(a, ff_neg(ff_mul(b, ff{q1, 0.0f})));
+    const float q2 = __fdiv_rn(r.hi, b.hi);
+    return fast_two_sum(q1, q2);
+}
+
+__device__ __forceinline__ ff ff_sqrt(ff a)
+{
+    if (!(a.hi > 0.0f)) return {0.0f, 0.0f};
+    const float s = __fsqrt_rn(a.hi);
+    const ff r = ff_add(a, ff_neg(ff_mul(ff{s, 0.0f}, ff{s, 0.0f})));
+    return fast_two_sum(s, __fdiv_rn(r.hi, __fmul_rn(2.0f, s)));
+}
+
+// Arithmetic of reduction and control scalars for element type T.
+template <typename T> struct Scal;
+template <> struct Scal<float> {
+    using S = ff;
+    static __device__ __forceinline__ S zero() { return {0.0f, 0.0f}; }
+    static __device__ __forceinline__ S of(float v) { return {v, 0.0f}; }
+    static __device__ __forceinline__ S add(S a, S b) { return ff_add(a, b); }
+    static __device__ __forceinline__ S addv(S a, float v) { return ff_add_f(a, v); }
+    static __device__ __forceinline__ S mul(S a, S b) { return ff_mul(a, b); }
+    static __device__ __forceinline__ S div(S a, S b) { return ff_div(a, b); }
+    static __device__ __forceinline__ S sqroot(S a) { return ff_sqrt(a); }
+    static __device__ __forceinline__ S shfl_down(S a, int o)
+    {
+        return {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+    }
+    static __device__ __forceinline__ float to_elem(S a) { return a.hi; }   // hi is hi + lo rounded
+    static __device__ __forceinline__ double to_double(S a) { return (double)a.hi + (double)a.lo; }
+    static __device__ __forceinline__ S from_double(double d)
+    {
+        const float hi = (float)d;
+        return {hi, (float)(d - (double)hi)};
+    }
+    static __device__ __forceinline__ bool le(S a, S b)
+    {
+        const S d = ff_add(a, ff_neg(b));
+        return d.hi < 0.0f || (d.hi == 0.0f && d.lo <= 0.0f);
+    }
+    static __device__ __forceinline__ bool positive(S a) { return a.hi > 0.0f; }
+    static __device__ __forceinline__ bool finite(S a) { return isfinite(a.hi) && isfinite(a.lo); }
+    static __device__ __forceinline__ S load_cg(const S *p)
+    {
+        const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+        return {v.x, v.y};
+    }
+};
+template <> struct Scal<double> {
+    using S = double;
+    static __device__ __forceinline__ S zero() { return 0.0; }
+    static __device__ __forceinline__ S of(double v) { return v; }
+    static __device__ __forceinline__ S add(S a, S b) { return a + b; }
+    static __device__ __forceinline__ S addv(S a, double v) { return a + v; }
+    static __device__ __forceinline__ S mul(S a, S b) { return a * b; }
+    static __device__ __forceinline__ S div(S a, S b) { return a / b; }
+    static __device__ __forceinline__ S sqroot(S a) { return a > 0.0 ? sqrt(a) : 0.0; }
+    static __device__ __forceinline__ S shfl_down(S a, int o) { return __shfl_down_sync(0xffffffffu, a, o); }
+    static __device__ __forceinline__ double to_elem(S a) { return a; }
+    static __device__ __forceinline__ double to_double(S a) { return a; }
+    static __device__ __forceinline__ S from_double(double d) { return d; }
+    static __device__ __forceinline__ bool le(S a, S b) { return a <= b; }
+    static __device__ __forceinline__ bool positive(S a) { return a > 0.0; }
+    static __device__ __forceinline__ bool finite(S a) { return isfinite(a); }
+    static __device__ __forceinline__ S load_cg(const S *p) { return __ldcg(p); }
+};
+
 // Sum over a warp; lane 0 holds the result (fixed tree order).
-__device__ __forceinline__ double warp_sum(double v)
+template <typename T>
+__device__ __forceinline__ typename Scal<T>::S warp_sum(typename Scal<T>::S v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v = Scal<T>::add(v, Scal<T>::shfl_down(v, o));
     return v;
 }
 
 // Deterministic CTA sum; every thread returns the same value.  `red` is a
-// shared array of MAXNW doubles.
-__device__ __forceinline__ double block_sum(double v, double *red)
+// shared array of MAXNW scalars.
+template <typename T>
+__device__ __forceinline__ typename Scal<T>::S block_sum(typename Scal<T>::S v, typename Scal<T>::S *red)
 {
-    v = warp_sum(v);
+    v = warp_sum<T>(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    typename Scal<T>::S t = Scal<T>::zero();
+    const int nw = blockDim.x >> 5;
+    for (int w = 0; w < nw; ++w) t = Scal<T>::add(t, red[w]);
+    return t;
+}
+
+// FP64 CTA sum (small control quantities: kernel norms, the Sobolev term).
+__device__ __forceinline__ double block_sum_d(double v, double *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
@@ -132,35 +273,39 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 // can overlap the copies with other work without holding registers.
 constexpr int GT_MAX = 512;          // largest grid the staging buffer holds
 
-__device__ __forceinline__ void cp_async8(double *dst, const double *src)
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
 }
 
-// warp 0 only
-__device__ __forceinline__ void grid_issue(const double *part, int n, double *sbuf)
+// warp 0 only; entries are 8-byte scalars
+template <typename T>
+__device__ __forceinline__ void grid_issue(const typename Scal<T>::S *part, int n, typename Scal<T>::S *sbuf)
 {
     for (int i = threadIdx.x & 31; i < n; i += 32) cp_async8(sbuf + i, part + i);
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 // warp 0 only; lane 0 returns the total
-__device__ __forceinline__ double grid_finish(int n, const double *sbuf)
+template <typename T>
+__device__ __forceinline__ typename Scal<T>::S grid_finish(int n, const typename Scal<T>::S *sbuf)
 {
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncwarp();
-    double s = 0.0;
-    for (int i = threadIdx.x & 31; i < n; i += 32) s += sbuf[i];
-    return warp_sum(s);
+    typename Scal<T>::S s = Scal<T>::zero();
+    for (int i = threadIdx.x & 31; i < n; i += 32) s = Scal<T>::add(s, sbuf[i]);
+    return warp_sum<T>(s);
 }
 
-__device__ __forceinline__ double grid_total(const double *part, int n, double *sbuf, double *bcast)
+template <typename T>
+__device__ __forceinline__ typename Scal<T>::S grid_total(const typename Scal<T>::S *part, int n,
+                                                          typename Scal<T>::S *sbuf, typename Scal<T>::S *bcast)
 {
     __syncthreads();
     if (threadIdx.x < 32) {
-        grid_issue(part, n, sbuf);
-        const double s = grid_finish(n, sbuf);
+        grid_issue<T>(part, n, sbuf);
+        const typename Scal<T>::S s = grid_finish<T>(n, sbuf);
         if (threadIdx.x == 0) *bcast = s;
     }
     __syncthreads();
@@ -302,6 +447,7 @@ struct Ctx {
     int PA, RA;                    // halo-r tile pitch (32 + 2r) and rows (MR + Kp - 1)
     long long *trace;              // optional: barrier timestamps of CTA 0 (arrive, leave)
     int trace_cap;
+    T alphaT, rpT;                 // alpha and the regulariser parameter in the element type
     long long N, HW;
     int reg;
     double alpha, rp, beta, w0, ddphi_max;

@@ -20,20 +20,24 @@ namespace adp {
 
 template <typename T>
 struct Eng {
+    using Sc = Scal<T>;
+    using S = typename Sc::S;      // reduction / control scalar (float-float or double)
     static constexpr int MR = Cfg<T>::MR;
     static constexpr int EWB = 8;  // element-wise phases: loads issued per batch per thread
     const Ctx<T> &cx;
     T *wF, *wT;                    // CTA: flipped / as-stored kernels, C x K x Kp (column-major)
     T *hA, *hB, *t1, *t2;          // this warp's tiles: two halo-r, two halo-1 (pitch 34)
-    double *red, *bcast, *tau, *gbuf;
+    S *red, *bcast, *gbuf;
+    double *redd;                  // FP64 CTA reductions of small control quantities
+    T *tau;                        // per-channel FISTA step 1/L_c
     int *sflag;
     int lane, warp, tid, nw, gw, TW;
     unsigned epoch;                // barriers passed so far (same in every thread)
     bool alive;                    // false once a barrier gave up or a status was raised
 
-    __device__ Eng(const Ctx<T> &c, unsigned char *smem, double *red_, double *bcast_, double *tau_, double *gbuf_,
+    __device__ Eng(const Ctx<T> &c, unsigned char *smem, S *red_, S *bcast_, double *redd_, T *tau_, S *gbuf_,
                    int *sflag_)
-        : cx(c), red(red_), bcast(bcast_), tau(tau_), gbuf(gbuf_), sflag(sflag_), epoch(0), alive(true)
+        : cx(c), red(red_), bcast(bcast_), gbuf(gbuf_), redd(redd_), tau(tau_), sflag(sflag_), epoch(0), alive(true)
     {
         lane = threadIdx.x & 31;
         warp = threadIdx.x >> 5;
@@ -104,12 +108,14 @@ struct Eng {
 
     // record this CTA's partial in a slot and return the grid total after a
     // barrier; every CTA obtains identical bits
-    __device__ double reduce(double mine, int slot)
+    __device__ S *partS(int slot) const { return reinterpret_cast<S *>(cx.part) + slot * gridDim.x; }
+
+    __device__ S reduce(S mine, int slot)
     {
-        const double cta = block_sum(mine, red);
-        if (tid == 0) cx.part[slot * gridDim.x + blockIdx.x] = cta;
-        if (!sync()) return 0.0;
-        return grid_total(cx.part + slot * gridDim.x, gridDim.x, gbuf, bcast);
+        const S cta = block_sum<T>(mine, red);
+        if (tid == 0) partS(slot)[blockIdx.x] = cta;
+        if (!sync()) return Sc::zero();
+        return grid_total<T>(partS(slot), gridDim.x, gbuf, bcast);
     }
 
     __device__ void stage_halo(T *dst, const T *src, long long cbase, int row0, int col0) const
@@ -137,9 +143,9 @@ struct Eng {
     // each in-image output (with its fetched operand) and returns its share of a
     // reduction (FP32 per strip, FP64 across strips).
     template <typename Stage, typename Fetch, typename Prep, typename Epi>
-    __device__ double pass(bool flip, Stage stage, Fetch fetch, Prep prep, Epi epi)
+    __device__ S pass(bool flip, Stage stage, Fetch fetch, Prep prep, Epi epi)
     {
-        double part = 0.0;
+        S part = Sc::zero();
         for (int s = gw; s < cx.nstrips; s += TW) {
             int c, row0, col0;
             strip_of(s, c, row0, col0);
@@ -164,7 +170,7 @@ struct Eng {
                 const int gi = row0 + m;
                 if (gi < cx.H && gj < cx.W) sum += epi(c, m, cbase + (long long)gi * cx.W + gj, acc[m], aux[m]);
             }
-            part += (double)sum;
+            part = Sc::addv(part, sum);
             __syncwarp();
         }
         return part;
@@ -175,7 +181,7 @@ struct Eng {
     // TV gradient at strip pixel (m, lane) of a halo-1 tile s (pitch 34)
     __device__ T tv_grad(const T *s, int m) const
     {
-        const T g = (T)cx.rp;
+        const T g = cx.rpT;
         const int o = (m + 1) * 34 + lane + 1;
         const T yc = s[o];
         return dphi<T>(cx.reg, yc - s[o - 1], g) - dphi<T>(cx.reg, s[o + 1] - yc, g) +
@@ -185,7 +191,7 @@ struct Eng {
     // D^T(phi''(D x) . D v) at strip pixel (m, lane); x in sx, v in sv (halo 1)
     __device__ T tv_hess(const T *sx, const T *sv, int m) const
     {
-        const T g = (T)cx.rp;
+        const T g = cx.rpT;
         const int o = (m + 1) * 34 + lane + 1;
         const T xc = sx[o], vc = sv[o];
         const T wl = ddphi<T>(cx.reg, xc - sx[o - 1], g);
@@ -218,9 +224,9 @@ struct Eng {
         load_weights(b);
         residual(x, cx.U);
         if (!sync()) return;
-        const T al = (T)cx.alpha;
+        const T al = cx.alphaT;
         const T *U = cx.U;
-        const double part = pass(
+        const S part = pass(
             false,
             [=](int, int row0, int col0, long long cbase) {
                 stage_halo(hA, U, cbase, row0, col0);
@@ -232,20 +238,20 @@ struct Eng {
                 if (out) out[g] = gr;
                 return gr * gr;
             });
-        const double ss = reduce(part, 0);
-        if (alive && tid == 0 && blockIdx.x == 0) cx.out->gradnorm = sqrt(ss);
+        const S ss = reduce(part, 0);
+        if (alive && tid == 0 && blockIdx.x == 0) cx.out->gradnorm = sqrt(Sc::to_double(ss));
     }
 
     // out = B^T B v + alpha D^T(phi''(D x) . D v) (weights of b loaded); returns
     // this CTA's share of <v, out>
-    __device__ double hess_vec(const T *x, const T *v, T *out)
+    __device__ S hess_vec(const T *x, const T *v, T *out)
     {
-        const T al = (T)cx.alpha;
+        const T al = cx.alphaT;
         T *U = cx.U;
         pass(true, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, v, cbase, row0, col0); },
              nofetch, [](int, int, int, long long) {},
              [=](int, int, long long g, T val, T) { U[g] = val; return T(0); });
-        if (!sync()) return 0.0;
+        if (!sync()) return Sc::zero();
         return pass(
             false,
             [=](int, int row0, int col0, long long cbase) {
@@ -262,14 +268,18 @@ struct Eng {
     }
 
     // 1/L_c for FISTA on channel c with kernel b: L_c = ||b_c||_1^2 + 8 alpha sup phi''
+    // (the l1 norm in the reduction scalar, the rest in FP64 by one thread)
     __device__ void compute_tau(const T *b)
     {
         const int KK = cx.K * cx.K;
         for (int c = 0; c < cx.C; ++c) {
-            double s = 0.0;
-            for (int e = tid; e < KK; e += blockDim.x) s += fabs((double)__ldcg(b + (long long)c * KK + e));
-            const double l1 = block_sum(s, red);
-            if (tid == 0) tau[c] = 1.0 / (l1 * l1 + 8.0 * cx.alpha * cx.ddphi_max);
+            S s = Sc::zero();
+            for (int e = tid; e < KK; e += blockDim.x) s = Sc::addv(s, fabs(__ldcg(b + (long long)c * KK + e)));
+            const S l1 = block_sum<T>(s, red);
+            if (tid == 0) {
+                const double l = Sc::to_double(l1);
+                tau[c] = (T)(1.0 / (l * l + 8.0 * cx.alpha * cx.ddphi_max));
+            }
         }
         __syncthreads();
     }
@@ -305,32 +315,34 @@ struct Eng {
         if (!sync()) return 0;
         T *xp = cx.X0, *xn = cx.X1, *yc = cx.Y0, *yn = cx.Y1, *U = cx.U;
         const T *y = cx.y;
-        const T al = (T)cx.alpha;
-        const double *tauc = tau;
+        const T al = cx.alphaT;
+        const T *tauc = tau;
         const T *result = nullptr;
-        double t = 1.0;
+        const S eps2 = Sc::from_double(eps * eps);
+        // momentum sequence t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2 in the control scalar
+        S t = Sc::of(1);
         bool pending = false;
         int k = 0;
         for (;; ++k) {
-            const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-            const T thn = (T)((t - 1.0) / tn);
+            const S tn = Sc::mul(Sc::addv(Sc::sqroot(Sc::addv(Sc::mul(Sc::of(4), Sc::mul(t, t)), 1)), 1), Sc::of(0.5));
+            const T thn = (T)Sc::to_elem(Sc::div(Sc::addv(t, -1), tn));
             const T *ycur = yc;
-            if (pending && warp == 0) grid_issue(cx.part + ((k - 1) & 1) * gridDim.x, gridDim.x, gbuf);
+            if (pending && warp == 0) grid_issue<T>(partS((k - 1) & 1), gridDim.x, gbuf);
             // phase A: U = B y_k - y
             pass(true, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, ycur, cbase, row0, col0); },
                  [=](long long g) { return __ldg(y + g); }, [](int, int, int, long long) {},
                  [=](int, int, long long g, T v, T yv) { U[g] = v - yv; return T(0); });
             if (pending) {
                 if (warp == 0) {
-                    const double s = grid_finish(gridDim.x, gbuf);
+                    const S s = grid_finish<T>(gridDim.x, gbuf);
                     if (lane == 0) *bcast = s;
                 }
                 __syncthreads();
-                const double gprev = sqrt(*bcast);
+                const S sprev = *bcast;
                 __syncthreads();
-                if (!isfinite(gprev)) { fail(ST_NONFINITE); return k - 1; }
-                if (gprev <= eps) {        // y_{k-1} passes: keep it, drop this pass A
-                    gn = gprev;
+                if (!Sc::finite(sprev)) { fail(ST_NONFINITE); return k - 1; }
+                if (Sc::le(sprev, eps2)) {     // y_{k-1} passes: keep it, drop this pass A
+                    gn = sqrt(Sc::to_double(sprev));
                     result = yn;
                     --k;
                     break;
@@ -341,7 +353,7 @@ struct Eng {
             // y_{k+1} = x_{k+1} + theta_{k+1} (x_{k+1} - x_k); ||G||^2
             T *xnl = xn, *ynl = yn;
             const T *xpl = xp;
-            const double part = pass(
+            const S part = pass(
                 false,
                 [=](int, int row0, int col0, long long cbase) {
                     stage_halo(hA, U, cbase, row0, col0);
@@ -350,18 +362,19 @@ struct Eng {
                 [=](long long g) { return __ldcg(xpl + g); }, [](int, int, int, long long) {},
                 [=](int c, int m, long long g, T v, T xpv) {
                     const T gr = v + al * tv_grad(t1, m);
-                    const T xnv = t1[(m + 1) * 34 + lane + 1] - (T)tauc[c] * gr;
+                    const T xnv = t1[(m + 1) * 34 + lane + 1] - tauc[c] * gr;
                     xnl[g] = xnv;
                     ynl[g] = xnv + thn * (xnv - xpv);
                     return gr * gr;
                 });
-            const double cta = block_sum(part, red);
-            if (tid == 0) cx.part[(k & 1) * gridDim.x + blockIdx.x] = cta;
+            const S cta = block_sum<T>(part, red);
+            if (tid == 0) partS(k & 1)[blockIdx.x] = cta;
             if (!sync()) return k;
             passes += 2;
             if (k >= max_iters) {          // cap: the norm of y_k is needed now
-                gn = sqrt(grid_total(cx.part + (k & 1) * gridDim.x, gridDim.x, gbuf, bcast));
-                if (!isfinite(gn)) { fail(ST_NONFINITE); return k; }
+                const S ss = grid_total<T>(partS(k & 1), gridDim.x, gbuf, bcast);
+                if (!Sc::finite(ss)) { fail(ST_NONFINITE); return k; }
+                gn = sqrt(Sc::to_double(ss));
                 result = yc;
                 break;
             }
@@ -390,7 +403,7 @@ struct Eng {
             const double dv = p < K - 1 ? (double)dker(b, base + pq + K) - d : 0.0;
             s += cx.w0 * d * d + dh * dh + dv * dv;
         }
-        return cx.beta * block_sum(s, red);
+        return cx.beta * block_sum_d(s, redd);
     }
 
     __device__ double grad_sobolev_elem(const T *b, int e) const
@@ -416,7 +429,7 @@ struct Eng {
         load_weights(cx.a);
         const T *y = cx.y;
         T *V = cx.V, *G = cx.G;
-        const double pg = pass(
+        const S pg = pass(
             true, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, x, cbase, row0, col0); },
             [=](long long g) { return __ldg(y + g); }, [](int, int, int, long long) {},
             [=](int, int, long long g, T v, T yv) {
@@ -424,9 +437,9 @@ struct Eng {
                 V[g] = e;
                 return e * e;
             });
-        const double gval = reduce(pg, 2);
+        const S gval = reduce(pg, 2);
         if (!alive) return;
-        const double pgg = pass(
+        const S pgg = pass(
             false, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, V, cbase, row0, col0); },
             nofetch, [](int, int, int, long long) {},
             [=](int, int, long long g, T v, T) {
@@ -434,11 +447,11 @@ struct Eng {
                 G[g] = gg;
                 return gg * gg;
             });
-        const double ggs = reduce(pgg, 3);
+        const S ggs = reduce(pgg, 3);
         if (!alive) return;
         passes += 2;
-        loss = gval + rb;
-        gxn = sqrt(ggs);
+        loss = Sc::to_double(gval) + rb;
+        gxn = sqrt(Sc::to_double(ggs));
         if (!isfinite(loss) || !isfinite(gxn)) fail(ST_NONFINITE);
     }
 
@@ -452,7 +465,7 @@ struct Eng {
         load_weights(b);
         T *R = cx.R, *HP = cx.HP, *U = cx.U;
         T *pc = cx.P0, *po = cx.P1;
-        double rrp = 0.0;
+        S rrp = Sc::zero();
         const long long N = cx.N, st = gstride();
         if (!zero_start) {
             hess_vec(x, Q, HP);
@@ -460,9 +473,9 @@ struct Eng {
             passes += 2;
         }
         {
-            T s = T(0);
             for (long long base = gstart(); base < N; base += EWB * st) {
                 T v[EWB];
+                T s = T(0);
 #pragma unroll
                 for (int u = 0; u < EWB; ++u) {
                     const long long i = base + u * st;
@@ -478,17 +491,18 @@ struct Eng {
                         s += v[u] * v[u];
                     }
                 }
+                rrp = Sc::addv(rrp, s);
             }
-            rrp = (double)s;
         }
-        double rr = reduce(rrp, 4);
+        S rr = reduce(rrp, 4);
         if (!alive) return 0;
+        const S delta2 = Sc::from_double(delta * delta);
         int it = 0;
         capped = 0;
         bool first = true;
         T beta = T(0);
-        const T al = (T)cx.alpha;
-        while (sqrt(rr) > delta && it < max_iters) {
+        const T al = cx.alphaT;
+        while (!Sc::le(rr, delta2) && it < max_iters) {
             // phase A: p (fused update unless first) and U = B p
             T *pcl = pc;
             const T *pol = po;
@@ -520,7 +534,7 @@ struct Eng {
                 [=](int, int, long long g, T v, T) { U[g] = v; return T(0); });
             if (!sync()) return it;
             // phase B: HP = B^T U + alpha D^T(phi''(D x) . D p); <p, HP>
-            const double php = reduce(
+            const S php = reduce(
                 pass(
                     false,
                     [=](int, int row0, int col0, long long cbase) {
@@ -537,12 +551,13 @@ struct Eng {
                 5);
             if (!alive) return it;
             passes += 2;
-            if (!isfinite(php)) { fail(ST_NONFINITE); return it; }
-            if (!(php > 0.0)) { capped = 1; break; }
-            const T a = (T)(rr / php);
-            T s = T(0);
+            if (!Sc::finite(php)) { fail(ST_NONFINITE); return it; }
+            if (!Sc::positive(php)) { capped = 1; break; }
+            const T a = (T)Sc::to_elem(Sc::div(rr, php));
+            S rn = Sc::zero();
             for (long long base = gstart(); base < N; base += EWB * st) {
                 T pv[EWB], qv[EWB], rv[EWB], hv[EWB];
+                T s = T(0);
 #pragma unroll
                 for (int u = 0; u < EWB; ++u) {
                     const long long i = base + u * st;
@@ -558,20 +573,21 @@ struct Eng {
                         s += r2 * r2;
                     }
                 }
+                rn = Sc::addv(rn, s);
             }
-            const double rr_new = reduce((double)s, 6);
+            const S rr_new = reduce(rn, 6);
             if (!alive) return it;
             ++it;
-            if (!isfinite(rr_new)) { fail(ST_NONFINITE); return it; }
-            if (sqrt(rr_new) <= delta) { rr = rr_new; break; }
-            beta = (T)(rr_new / rr);
+            if (!Sc::finite(rr_new)) { fail(ST_NONFINITE); return it; }
+            if (Sc::le(rr_new, delta2)) { rr = rr_new; break; }
+            beta = (T)Sc::to_elem(Sc::div(rr_new, rr));
             rr = rr_new;
             po = pc;
             pc = (pc == cx.P0) ? cx.P1 : cx.P0;
             first = false;
         }
-        res = sqrt(rr);
-        if (res > delta) capped = 1;
+        res = sqrt(Sc::to_double(rr));
+        if (!Sc::le(rr, delta2)) capped = 1;
         return it;
     }
 
@@ -585,8 +601,9 @@ struct Eng {
         T *U = cx.U, *V = cx.V;
         const int r = cx.r, K = cx.K, KK = K * K, H = cx.H, W = cx.W;
         const int CKK = cx.C * KK;
-        double *zp = cx.zpart + (long long)gw * CKK;
-        for (int e = lane; e < CKK; e += 32) zp[e] = 0.0;
+        S *zall = reinterpret_cast<S *>(cx.zpart);
+        S *zp = zall + (long long)gw * CKK;
+        for (int e = lane; e < CKK; e += 32) zp[e] = Sc::zero();
         // phase K1: U = B v, V = B x - y
         for (int s = gw; s < cx.nstrips; s += TW) {
             int c, row0, col0;
@@ -594,19 +611,25 @@ struct Eng {
             const long long cbase = (long long)c * cx.HW;
             stage_halo(hA, v, cbase, row0, col0);
             stage_halo(hB, x, cbase, row0, col0);
+            const int gj = col0 + lane;
+            T yv[MR];
+#pragma unroll
+            for (int m = 0; m < MR; ++m) {
+                const int gi = row0 + m;
+                yv[m] = (gi < H && gj < W) ? __ldg(y + cbase + (long long)gi * W + gj) : T(0);
+            }
             cp_async_wait_all();
             __syncwarp();
             T au[MR], av[MR];
             corr(hA, true, c, au);
             corr(hB, true, c, av);
-            const int gj = col0 + lane;
 #pragma unroll
             for (int m = 0; m < MR; ++m) {
                 const int gi = row0 + m;
                 if (gi < H && gj < W) {
                     const long long g = cbase + (long long)gi * W + gj;
                     U[g] = au[m];
-                    V[g] = av[m] - __ldg(y + g);
+                    V[g] = av[m] - yv[m];
                 }
             }
             __syncwarp();
@@ -634,9 +657,9 @@ struct Eng {
             __syncwarp();
             for (int u = lane; u < units; u += 32) {
                 const int p = u / nqb, q0 = (u - p * nqb) * QB;
-                double acc[QB];
+                S acc[QB];
 #pragma unroll
-                for (int k = 0; k < QB; ++k) acc[k] = 0.0;
+                for (int k = 0; k < QB; ++k) acc[k] = Sc::zero();
                 for (int m = 0; m < MR; ++m) {
                     const T *rx = hA + (m + 2 * r - p) * cx.PA;
                     const T *rv = hB + (m + 2 * r - p) * cx.PA;
@@ -664,28 +687,35 @@ struct Eng {
                         }
                     }
 #pragma unroll
-                    for (int k = 0; k < QB; ++k) acc[k] += (double)af[k];
+                    for (int k = 0; k < QB; ++k) acc[k] = Sc::addv(acc[k], af[k]);
                 }
 #pragma unroll
                 for (int k = 0; k < QB; ++k)
-                    if (q0 + k < K) zp[c * KK + p * K + q0 + k] += acc[k];
+                    if (q0 + k < K) zp[c * KK + p * K + q0 + k] = Sc::add(zp[c * KK + p * K + q0 + k], acc[k]);
             }
             __syncwarp();
         }
         if (!sync()) return 0.0;
-        // phase K3: fixed-order sum over warps, sign, Sobolev term
-        for (long long e = gstart(); e < CKK; e += gstride()) {
-            double s = 0.0;
-            for (int w = 0; w < TW; ++w) s += __ldcg(cx.zpart + (long long)w * CKK + e);
-            double zz = negate ? -s : s;
-            if (add_r) zz += grad_sobolev_elem(b, (int)e);
-            zout[e] = (T)zz;
+        // phase K3: one warp per kernel entry sums the per-warp rows in a fixed
+        // order (lane l takes rows l, l+32, ...; then the shuffle tree), then
+        // applies the sign and the Sobolev term
+        for (int e = gw; e < CKK; e += TW) {
+            S s = Sc::zero();
+#pragma unroll 4
+            for (int w = lane; w < TW; w += 32) s = Sc::add(s, Sc::load_cg(zall + (long long)w * CKK + e));
+            s = warp_sum<T>(s);
+            if (lane == 0) {
+                double zz = Sc::to_double(s);
+                if (negate) zz = -zz;
+                if (add_r) zz += grad_sobolev_elem(b, e);
+                zout[e] = (T)zz;
+            }
         }
         passes += 4;   // B v, B x and the two lag correlations
         if (!sync()) return 0.0;
-        double s = 0.0;
-        for (int e = tid; e < CKK; e += blockDim.x) { const double zv = (double)__ldcg(zout + e); s += zv * zv; }
-        return block_sum(s, red);
+        S s = Sc::zero();
+        for (int e = tid; e < CKK; e += blockDim.x) { const T zv = __ldcg(zout + e); s = Sc::addv(s, zv * zv); }
+        return Sc::to_double(block_sum<T>(s, red));
     }
 
     // ------------------------------------------------------------ MAID
@@ -774,12 +804,14 @@ __global__ void __launch_bounds__(MAXNW * 32, 1) adp_kernel(const __grid_constan
                                                          const __grid_constant__ Job<T> jb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[MAXNW];
-    __shared__ double bcast;
-    __shared__ double tau[MAXC];
-    __shared__ double gbuf[GT_MAX];
+    using S = typename Scal<T>::S;
+    __shared__ S red[MAXNW];
+    __shared__ S bcast;
+    __shared__ double redd[MAXNW];
+    __shared__ T tau[MAXC];
+    __shared__ __align__(16) S gbuf[GT_MAX];
     __shared__ int sflag;
-    Eng<T> e(cx, smem_raw, red, &bcast, tau, gbuf, &sflag);
+    Eng<T> e(cx, smem_raw, red, &bcast, redd, tau, gbuf, &sflag);
     const bool lead = threadIdx.x == 0 && blockIdx.x == 0;
     long long passes = 0;
     switch (jb.mode) {
