@@ -78,7 +78,7 @@ static Ctx<T> make_ctx(const adp_problem *p)
     c.HW = (long long)q.H * q.W; c.N = c.HW * q.C;
     c.reg = q.reg; c.alpha = q.alpha; c.rp = q.reg_param; c.beta = q.beta; c.w0 = q.sobolev_w0;
     c.ddphi_max = q.reg == ADP_REG_QUAD ? 1.0 : 1.0 / q.reg_param;
-    c.alphaT = (T)q.alpha; c.rpT = (T)q.reg_param;
+    c.alphaT = (T)q.alpha; c.rpT = (T)q.reg_param; c.irpT = (T)(1.0 / q.reg_param);
     c.y = (const T *)p->y; c.a = (const T *)p->a;
     T **im[12] = {&c.X0, &c.X1, &c.Y0, &c.Y1, &c.U, &c.V, &c.G, &c.R, &c.P0, &c.P1, &c.HP, &c.XT};
     for (int i = 0; i < 12; ++i) *im[i] = (T *)p->img[i];

@@ -157,20 +157,23 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b)
     return fast_two_sum(p, e);
 }
 
+// Quotient and square root: a fast first approximation, then one correction
+// from the exact residual (computed with TwoProd), which restores float-float
+// accuracy whatever the few-ulp error of the first step.
 __device__ __forceinline__ ff ff_div(ff a, ff b)
 {
-    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const float q1 = __fdividef(a.hi, b.hi);
     const ff r = ff_add(a, ff_neg(ff_mul(b, ff{q1, 0.0f})));
-    const float q2 = __fdiv_rn(r.hi, b.hi);
+    const float q2 = __fdividef(r.hi, b.hi);
     return fast_two_sum(q1, q2);
 }
 
 __device__ __forceinline__ ff ff_sqrt(ff a)
 {
     if (!(a.hi > 0.0f)) return {0.0f, 0.0f};
-    const float s = __fsqrt_rn(a.hi);
+    const float s = __fmul_rn(a.hi, rsqrtf(a.hi));
     const ff r = ff_add(a, ff_neg(ff_mul(ff{s, 0.0f}, ff{s, 0.0f})));
-    return fast_two_sum(s, __fdiv_rn(r.hi, __fmul_rn(2.0f, s)));
+    return fast_two_sum(s, __fdividef(r.hi, __fmul_rn(2.0f, s)));
 }
 
 // Arithmetic of reduction and control scalars for element type T.
@@ -411,20 +414,25 @@ __device__ __forceinline__ void corr_strip(const T *__restrict__ s, int pitch, c
     if (ci < total) comp(xa, wa);
 }
 
-// phi' and phi'' of the regularisers (reg: 0 Huber, 1 sqrt, 2 quadratic).
+// phi' and phi'' of the regularisers (reg: 0 Huber, 1 sqrt, 2 quadratic);
+// ig = 1/gamma for the Huber branch.  The FP32 path uses the reciprocal and the
+// hardware reciprocal square root (a few ulp) instead of IEEE division.
+__device__ __forceinline__ float rsqrt_t(float s) { return rsqrtf(s); }
+__device__ __forceinline__ double rsqrt_t(double s) { return 1.0 / sqrt(s); }
+
 template <typename T>
-__device__ __forceinline__ T dphi(int reg, T t, T g)
+__device__ __forceinline__ T dphi(int reg, T t, T g, T ig)
 {
-    if (reg == 0) return fabs(t) <= g ? t / g : (t > T(0) ? T(1) : T(-1));
-    if (reg == 1) return t / sqrt(t * t + g * g);
+    if (reg == 0) return fabs(t) <= g ? t * ig : (t > T(0) ? T(1) : T(-1));
+    if (reg == 1) return t * rsqrt_t(t * t + g * g);
     return t;
 }
 
 template <typename T>
-__device__ __forceinline__ T ddphi(int reg, T t, T g)
+__device__ __forceinline__ T ddphi(int reg, T t, T g, T ig)
 {
-    if (reg == 0) return fabs(t) <= g ? T(1) / g : T(0);
-    if (reg == 1) { const T s = t * t + g * g; return g * g / (s * sqrt(s)); }
+    if (reg == 0) return fabs(t) <= g ? ig : T(0);
+    if (reg == 1) { const T s = t * t + g * g; const T rs = rsqrt_t(s); return g * g * rs * rs * rs; }
     return T(1);
 }
 
@@ -447,7 +455,7 @@ struct Ctx {
     int PA, RA;                    // halo-r tile pitch (32 + 2r) and rows (MR + Kp - 1)
     long long *trace;              // optional: barrier timestamps of CTA 0 (arrive, leave)
     int trace_cap;
-    T alphaT, rpT;                 // alpha and the regulariser parameter in the element type
+    T alphaT, rpT, irpT;           // alpha, the regulariser parameter and its reciprocal (element type)
     long long N, HW;
     int reg;
     double alpha, rp, beta, w0, ddphi_max;
@@ -484,7 +492,8 @@ __host__ __device__ inline void smem_layout(int C, int K, int nw, int &w_elems, 
     const int r = (K - 1) / 2, Kp = round_up(K, Cfg<T>::PC);
     const int PA = 32 + 2 * r, RA = MR + Kp - 1;
     w_elems = round_up(2 * C * Kp * K, 4);                   // flipped and as-stored kernels
-    warp_elems = round_up(2 * RA * PA + 2 * (MR + 2) * 34, 4);   // two halo-r tiles, two halo-1 tiles
+    // two halo-r tiles, two halo-1 tiles, one interior tile of epilogue operands
+    warp_elems = round_up(2 * RA * PA + 2 * (MR + 2) * 34 + MR * 32, 4);
     total = w_elems + nw * warp_elems;
 }
 

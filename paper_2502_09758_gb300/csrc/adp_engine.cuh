@@ -27,6 +27,7 @@ struct Eng {
     const Ctx<T> &cx;
     T *wF, *wT;                    // CTA: flipped / as-stored kernels, C x K x Kp (column-major)
     T *hA, *hB, *t1, *t2;          // this warp's tiles: two halo-r, two halo-1 (pitch 34)
+    T *tF;                         // this warp's MR x 32 tile of per-pixel epilogue operands
     S *red, *bcast, *gbuf;
     double *redd;                  // FP64 CTA reductions of small control quantities
     T *tau;                        // per-channel FISTA step 1/L_c
@@ -54,6 +55,7 @@ struct Eng {
         hB = hA + cx.RA * cx.PA;
         t1 = hB + cx.RA * cx.PA;
         t2 = t1 + (MR + 2) * 34;
+        tF = t2 + (MR + 2) * 34;
     }
 
     __device__ bool sync()
@@ -137,13 +139,14 @@ struct Eng {
     }
 
     // One convolution pass over all strips.  stage() issues the async copies of
-    // the strip (halo-r input into hA, extra tiles as needed); fetch(g) loads a
-    // per-pixel operand of the epilogue, issued while the copies are in flight;
-    // prep() runs on the staged tiles before the correlation; epi() consumes
-    // each in-image output (with its fetched operand) and returns its share of a
-    // reduction (FP32 per strip, FP64 across strips).
-    template <typename Stage, typename Fetch, typename Prep, typename Epi>
-    __device__ S pass(bool flip, Stage stage, Fetch fetch, Prep prep, Epi epi)
+    // the strip (halo-r input into hA, extra tiles as needed); when fsrc is not
+    // null the strip's own pixels of fsrc (a per-pixel operand of the
+    // epilogue) are staged into tF with the same batch of copies; prep() runs
+    // on the staged tiles before the correlation; epi() consumes each in-image
+    // output (with its staged operand) and returns its share of a reduction
+    // (in the element type per strip, in the reduction scalar across strips).
+    template <typename Stage, typename Prep, typename Epi>
+    __device__ S pass(bool flip, Stage stage, const T *fsrc, Prep prep, Epi epi)
     {
         S part = Sc::zero();
         for (int s = gw; s < cx.nstrips; s += TW) {
@@ -151,13 +154,7 @@ struct Eng {
             strip_of(s, c, row0, col0);
             const long long cbase = (long long)c * cx.HW;
             stage(c, row0, col0, cbase);
-            const int gj = col0 + lane;
-            T aux[MR];
-#pragma unroll
-            for (int m = 0; m < MR; ++m) {
-                const int gi = row0 + m;
-                aux[m] = (gi < cx.H && gj < cx.W) ? fetch(cbase + (long long)gi * cx.W + gj) : T(0);
-            }
+            if (fsrc) warp_stage(tF, 32, MR, 32, fsrc, cbase, row0, col0, cx.H, cx.W, lane);
             cp_async_wait_all();
             __syncwarp();
             prep(c, row0, col0, cbase);
@@ -165,10 +162,12 @@ struct Eng {
             T acc[MR];
             corr(hA, flip, c, acc);
             T sum = T(0);
+            const int gj = col0 + lane;
 #pragma unroll
             for (int m = 0; m < MR; ++m) {
                 const int gi = row0 + m;
-                if (gi < cx.H && gj < cx.W) sum += epi(c, m, cbase + (long long)gi * cx.W + gj, acc[m], aux[m]);
+                if (gi < cx.H && gj < cx.W)
+                    sum += epi(c, m, cbase + (long long)gi * cx.W + gj, acc[m], tF[m * 32 + lane]);
             }
             part = Sc::addv(part, sum);
             __syncwarp();
@@ -176,28 +175,26 @@ struct Eng {
         return part;
     }
 
-    static __device__ T nofetch(long long) { return T(0); }
-
     // TV gradient at strip pixel (m, lane) of a halo-1 tile s (pitch 34)
     __device__ T tv_grad(const T *s, int m) const
     {
-        const T g = cx.rpT;
+        const T g = cx.rpT, ig = cx.irpT;
         const int o = (m + 1) * 34 + lane + 1;
         const T yc = s[o];
-        return dphi<T>(cx.reg, yc - s[o - 1], g) - dphi<T>(cx.reg, s[o + 1] - yc, g) +
-               dphi<T>(cx.reg, yc - s[o - 34], g) - dphi<T>(cx.reg, s[o + 34] - yc, g);
+        return dphi<T>(cx.reg, yc - s[o - 1], g, ig) - dphi<T>(cx.reg, s[o + 1] - yc, g, ig) +
+               dphi<T>(cx.reg, yc - s[o - 34], g, ig) - dphi<T>(cx.reg, s[o + 34] - yc, g, ig);
     }
 
     // D^T(phi''(D x) . D v) at strip pixel (m, lane); x in sx, v in sv (halo 1)
     __device__ T tv_hess(const T *sx, const T *sv, int m) const
     {
-        const T g = cx.rpT;
+        const T g = cx.rpT, ig = cx.irpT;
         const int o = (m + 1) * 34 + lane + 1;
         const T xc = sx[o], vc = sv[o];
-        const T wl = ddphi<T>(cx.reg, xc - sx[o - 1], g);
-        const T wr = ddphi<T>(cx.reg, sx[o + 1] - xc, g);
-        const T wu = ddphi<T>(cx.reg, xc - sx[o - 34], g);
-        const T wd = ddphi<T>(cx.reg, sx[o + 34] - xc, g);
+        const T wl = ddphi<T>(cx.reg, xc - sx[o - 1], g, ig);
+        const T wr = ddphi<T>(cx.reg, sx[o + 1] - xc, g, ig);
+        const T wu = ddphi<T>(cx.reg, xc - sx[o - 34], g, ig);
+        const T wd = ddphi<T>(cx.reg, sx[o + 34] - xc, g, ig);
         return wl * (vc - sv[o - 1]) - wr * (sv[o + 1] - vc) + wu * (vc - sv[o - 34]) - wd * (sv[o + 34] - vc);
     }
 
@@ -206,7 +203,7 @@ struct Eng {
     {
         load_weights(b);
         pass(!transpose, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, x, cbase, row0, col0); },
-             nofetch, [](int, int, int, long long) {},
+             nullptr, [](int, int, int, long long) {},
              [=](int, int, long long g, T v, T) { out[g] = v; return T(0); });
     }
 
@@ -215,7 +212,7 @@ struct Eng {
     {
         const T *y = cx.y;
         pass(true, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, x, cbase, row0, col0); },
-             [=](long long g) { return __ldg(y + g); }, [](int, int, int, long long) {},
+             y, [](int, int, int, long long) {},
              [=](int, int, long long g, T v, T yv) { U[g] = v - yv; return T(0); });
     }
 
@@ -232,7 +229,7 @@ struct Eng {
                 stage_halo(hA, U, cbase, row0, col0);
                 stage_halo1(t1, x, cbase, row0, col0);
             },
-            nofetch, [](int, int, int, long long) {},
+            nullptr, [](int, int, int, long long) {},
             [=](int, int m, long long g, T v, T) {
                 const T gr = v + al * tv_grad(t1, m);
                 if (out) out[g] = gr;
@@ -249,7 +246,7 @@ struct Eng {
         const T al = cx.alphaT;
         T *U = cx.U;
         pass(true, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, v, cbase, row0, col0); },
-             nofetch, [](int, int, int, long long) {},
+             nullptr, [](int, int, int, long long) {},
              [=](int, int, long long g, T val, T) { U[g] = val; return T(0); });
         if (!sync()) return Sc::zero();
         return pass(
@@ -259,7 +256,7 @@ struct Eng {
                 stage_halo1(t1, x, cbase, row0, col0);
                 stage_halo1(t2, v, cbase, row0, col0);
             },
-            nofetch, [](int, int, int, long long) {},
+            nullptr, [](int, int, int, long long) {},
             [=](int, int m, long long g, T val, T) {
                 const T hv = val + al * tv_hess(t1, t2, m);
                 out[g] = hv;
@@ -300,6 +297,12 @@ struct Eng {
         }
     }
 
+    // t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, the FISTA momentum sequence
+    __device__ S next_t(S t) const
+    {
+        return Sc::mul(Sc::addv(Sc::sqroot(Sc::addv(Sc::mul(Sc::of(4), Sc::mul(t, t)), 1)), 1), Sc::of(0.5));
+    }
+
     // FISTA (Algorithm 1, step 1) from x_in to x_out: returns updates made.
     // The momentum theta_{k+1} = (t_k - 1)/t_{k+1} does not depend on the data,
     // so pass B writes both x_{k+1} and y_{k+1}.  The stopping test on
@@ -320,17 +323,19 @@ struct Eng {
         const T *result = nullptr;
         const S eps2 = Sc::from_double(eps * eps);
         // momentum sequence t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2 in the control scalar
+        // theta_{k+1} for the first iteration (t_0 = 1); later ones are computed
+        // while a barrier is pending
         S t = Sc::of(1);
+        S tn = next_t(t);
+        T thn = (T)Sc::to_elem(Sc::div(Sc::addv(t, -1), tn));
         bool pending = false;
         int k = 0;
         for (;; ++k) {
-            const S tn = Sc::mul(Sc::addv(Sc::sqroot(Sc::addv(Sc::mul(Sc::of(4), Sc::mul(t, t)), 1)), 1), Sc::of(0.5));
-            const T thn = (T)Sc::to_elem(Sc::div(Sc::addv(t, -1), tn));
             const T *ycur = yc;
             if (pending && warp == 0) grid_issue<T>(partS((k - 1) & 1), gridDim.x, gbuf);
             // phase A: U = B y_k - y
             pass(true, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, ycur, cbase, row0, col0); },
-                 [=](long long g) { return __ldg(y + g); }, [](int, int, int, long long) {},
+                 y, [](int, int, int, long long) {},
                  [=](int, int, long long g, T v, T yv) { U[g] = v - yv; return T(0); });
             if (pending) {
                 if (warp == 0) {
@@ -359,7 +364,7 @@ struct Eng {
                     stage_halo(hA, U, cbase, row0, col0);
                     stage_halo1(t1, ycur, cbase, row0, col0);
                 },
-                [=](long long g) { return __ldcg(xpl + g); }, [](int, int, int, long long) {},
+                xpl, [](int, int, int, long long) {},
                 [=](int c, int m, long long g, T v, T xpv) {
                     const T gr = v + al * tv_grad(t1, m);
                     const T xnv = t1[(m + 1) * 34 + lane + 1] - tauc[c] * gr;
@@ -369,6 +374,10 @@ struct Eng {
                 });
             const S cta = block_sum<T>(part, red);
             if (tid == 0) partS(k & 1)[blockIdx.x] = cta;
+            // momentum of the next iteration, before waiting on the barrier
+            const S t_next = tn;
+            const S tn_next = next_t(t_next);
+            const T thn_next = (T)Sc::to_elem(Sc::div(Sc::addv(t_next, -1), tn_next));
             if (!sync()) return k;
             passes += 2;
             if (k >= max_iters) {          // cap: the norm of y_k is needed now
@@ -379,7 +388,9 @@ struct Eng {
                 break;
             }
             pending = true;
-            t = tn;
+            t = t_next;
+            tn = tn_next;
+            thn = thn_next;
             T *tmp = xp; xp = xn; xn = tmp;
             tmp = yc; yc = yn; yn = tmp;
         }
@@ -431,7 +442,7 @@ struct Eng {
         T *V = cx.V, *G = cx.G;
         const S pg = pass(
             true, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, x, cbase, row0, col0); },
-            [=](long long g) { return __ldg(y + g); }, [](int, int, int, long long) {},
+            y, [](int, int, int, long long) {},
             [=](int, int, long long g, T v, T yv) {
                 const T e = v - yv;
                 V[g] = e;
@@ -441,7 +452,7 @@ struct Eng {
         if (!alive) return;
         const S pgg = pass(
             false, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, V, cbase, row0, col0); },
-            nofetch, [](int, int, int, long long) {},
+            nullptr, [](int, int, int, long long) {},
             [=](int, int, long long g, T v, T) {
                 const T gg = T(2) * v;
                 G[g] = gg;
@@ -518,7 +529,7 @@ struct Eng {
                         stage_halo(hB, pol, cbase, row0, col0);
                     }
                 },
-                nofetch,
+                nullptr,
                 [=](int, int row0, int col0, long long cbase) {
                     if (fst) return;
                     const int n = cx.RA * cx.PA;
@@ -542,7 +553,7 @@ struct Eng {
                         stage_halo1(t1, x, cbase, row0, col0);
                         stage_halo1(t2, pcl, cbase, row0, col0);
                     },
-                    nofetch, [](int, int, int, long long) {},
+                    nullptr, [](int, int, int, long long) {},
                     [=](int, int m, long long g, T v, T) {
                         const T hv = v + al * tv_hess(t1, t2, m);
                         HP[g] = hv;

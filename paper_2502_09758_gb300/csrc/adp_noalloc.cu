@@ -120,7 +120,7 @@ adp_status run_noalloc(const adp_params &q, DeviceSetup &ds, const void *y, cons
     c.HW = (long long)q.H * q.W; c.N = c.HW * q.C;
     c.reg = q.reg; c.alpha = q.alpha; c.rp = q.reg_param; c.beta = q.beta; c.w0 = q.sobolev_w0;
     c.ddphi_max = q.reg == ADP_REG_QUAD ? 1.0 : 1.0 / q.reg_param;
-    c.alphaT = (T)q.alpha; c.rpT = (T)q.reg_param;
+    c.alphaT = (T)q.alpha; c.rpT = (T)q.reg_param; c.irpT = (T)(1.0 / q.reg_param);
     c.y = (const T *)y; c.a = nullptr;
     c.bar = (unsigned *)base;
     c.out = (DevOut *)(base + kHeadBytes);
