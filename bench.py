@@ -216,6 +216,21 @@ def plain_maid_run(prob, a, y):
     return (time.perf_counter() - t0) * 1e3, ups, b, x
 
 
+def reduce_over_ranks(tot_ms, units, device=None):
+    """Whole-job figures of independent replicas: the slowest rank's time and
+    the units all ranks processed (no data-path collective; this is the only
+    exchange, once, after the timed region)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(tot_ms), float(units)
+    t = torch.tensor([tot_ms, units], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -269,14 +284,7 @@ def run_ours(args):
 
     tot_ms = sum(run_ms)
     units = N * iters
-    if world > 1:
-        t = torch.tensor([tot_ms, units], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        tot_ms_max, units_all = float(tmax[0]), float(t[1])
-    else:
-        tot_ms_max, units_all = tot_ms, float(units)
+    tot_ms_max, units_all = reduce_over_ranks(tot_ms, units, dev)
     value = units_all / (tot_ms_max / 1e3) / 1e6
 
     xr, br = x.double().cpu().numpy(), b.double().cpu().numpy()

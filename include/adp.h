@@ -195,6 +195,13 @@ double adp_last_kernel_ms(adp_problem *p);
 adp_status adp_lower_solve_noalloc(const adp_params *params, const void *y, const void *b, void *x, double eps,
                                    int max_iters, void *stream, int *iters, double *gradnorm);
 
+/* Diagnostic of the failure path (no counterpart in the paper): one launch
+ * of p's kernel in which CTA 0 never arrives at a grid barrier, so the bounded
+ * wait of every other CTA runs out after the problem's wait_timeout_s.  The
+ * expected result is ADP_ETIMEOUT, returned without a fault, with p and the
+ * CUDA context still usable.  ADP_EINVAL when p's launch has a single CTA. */
+adp_status adp_selftest_wait_timeout(adp_problem *p);
+
 /* Tracing (diagnostics).  With cap > 0, later calls on p record, for the first
  * cap grid barriers of each launch, the device global timer (ns) when CTA 0
  * arrived at and left the barrier; cap = 0 turns tracing off.  Allocates (and

@@ -88,6 +88,10 @@ def _L():
             "orc_maid_step": (ct.c_int, [P, ct.POINTER(MaidState), dp, dp, dp, dp, dp]),
             "orc_L_gx": (d, [P, dp]),
             "orc_norm": (d, [dp, ct.c_long]),
+            "orc_conv_at": (d, [P, dp, dp, ct.c_int, ct.c_int, ct.c_int]),
+            "orc_conv_adj_at": (d, [P, dp, dp, ct.c_int, ct.c_int, ct.c_int]),
+            "orc_grad_h_at": (d, [P, dp, dp, dp, ct.c_int, ct.c_int, ct.c_int]),
+            "orc_hess_h_vec_at": (d, [P, dp, dp, dp, ct.c_int, ct.c_int, ct.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -142,6 +146,27 @@ class Problem:
         out = np.empty(self.img_shape)
         _L().orc_conv_adj(self._s(), _ptr(b), _ptr(z), _ptr(out))
         return out
+
+    # single outputs at sampled indices (rows of ``idx`` are (c, i, j))
+    def conv_at(self, b, x, idx):
+        b, x = _f64(b), _f64(x)
+        return np.array([_L().orc_conv_at(self._s(), _ptr(b), _ptr(x), int(c), int(i), int(j))
+                         for c, i, j in idx])
+
+    def conv_adj_at(self, b, z, idx):
+        b, z = _f64(b), _f64(z)
+        return np.array([_L().orc_conv_adj_at(self._s(), _ptr(b), _ptr(z), int(c), int(i), int(j))
+                         for c, i, j in idx])
+
+    def grad_h_at(self, b, x, y, idx):
+        b, x, y = _f64(b), _f64(x), _f64(y)
+        return np.array([_L().orc_grad_h_at(self._s(), _ptr(b), _ptr(x), _ptr(y), int(c), int(i), int(j))
+                         for c, i, j in idx])
+
+    def hess_h_vec_at(self, b, x, v, idx):
+        b, x, v = _f64(b), _f64(x), _f64(v)
+        return np.array([_L().orc_hess_h_vec_at(self._s(), _ptr(b), _ptr(x), _ptr(v), int(c), int(i), int(j))
+                         for c, i, j in idx])
 
     def _unary(self, name, x):
         x = _f64(x)

@@ -282,6 +282,85 @@ void orc_hess_h_vec(const orc_prob *p, const double *b, const double *x, const d
     free(u); free(t);
 }
 
+/* ------------------------------------------------- single outputs (sampling)
+ * The same definitions evaluated at one pixel, for checks at image sizes where
+ * the whole-image functions above would take too long.  Each restates its
+ * whole-image counterpart at one output index. */
+
+/* (B x)[c,i,j], Eq. 2.4 */
+double orc_conv_at(const orc_prob *p, const double *b, const double *x, int c, int i, int j)
+{
+    int H = p->H, W = p->W, K = p->K, r = (K - 1) / 2;
+    double s = 0.0;
+    for (int pp = 0; pp < K; ++pp)
+        for (int qq = 0; qq < K; ++qq)
+            s += b[((size_t)c * K + pp) * K + qq] *
+                 x[((size_t)c * H + wrap(i - pp + r, H)) * W + wrap(j - qq + r, W)];
+    return s;
+}
+
+/* (B^T z)[c,i,j] */
+double orc_conv_adj_at(const orc_prob *p, const double *b, const double *z, int c, int i, int j)
+{
+    int H = p->H, W = p->W, K = p->K, r = (K - 1) / 2;
+    double s = 0.0;
+    for (int pp = 0; pp < K; ++pp)
+        for (int qq = 0; qq < K; ++qq)
+            s += b[((size_t)c * K + pp) * K + qq] *
+                 z[((size_t)c * H + wrap(i + pp - r, H)) * W + wrap(j + qq - r, W)];
+    return s;
+}
+
+/* value of image u at (c, i, j) with periodic indices */
+static double at(const orc_prob *p, const double *u, int c, int i, int j)
+{
+    return u[((size_t)c * p->H + wrap(i, p->H)) * p->W + wrap(j, p->W)];
+}
+
+/* (grad J)[c,i,j] = phi'(x_ij - x_i,j-1) - phi'(x_i,j+1 - x_ij)
+ *                 + phi'(x_ij - x_i-1,j) - phi'(x_i+1,j - x_ij),
+ * the entry of D_h^T phi'(D_h x) + D_v^T phi'(D_v x) at one pixel */
+static double gradJ_at(const orc_prob *p, const double *x, int c, int i, int j)
+{
+    double xc = at(p, x, c, i, j);
+    return orc_dphi(p, xc - at(p, x, c, i, j - 1)) - orc_dphi(p, at(p, x, c, i, j + 1) - xc) +
+           orc_dphi(p, xc - at(p, x, c, i - 1, j)) - orc_dphi(p, at(p, x, c, i + 1, j) - xc);
+}
+
+/* (grad_x h)[c,i,j] = (B^T (B x - y))[c,i,j] + alpha (grad J)[c,i,j]; the
+ * residual B x - y is formed at each of the K^2 pixels the adjoint reads */
+double orc_grad_h_at(const orc_prob *p, const double *b, const double *x, const double *y, int c, int i, int j)
+{
+    int K = p->K, r = (K - 1) / 2;
+    double s = 0.0;
+    for (int pp = 0; pp < K; ++pp)
+        for (int qq = 0; qq < K; ++qq) {
+            int ii = wrap(i + pp - r, p->H), jj = wrap(j + qq - r, p->W);
+            double u = orc_conv_at(p, b, x, c, ii, jj) - at(p, y, c, ii, jj);
+            s += b[((size_t)c * K + pp) * K + qq] * u;
+        }
+    return s + p->alpha * gradJ_at(p, x, c, i, j);
+}
+
+/* (grad^2_x h v)[c,i,j] = (B^T B v)[c,i,j] + alpha (D^T(phi''(D x) . D v))[c,i,j] */
+double orc_hess_h_vec_at(const orc_prob *p, const double *b, const double *x, const double *v, int c, int i,
+                         int j)
+{
+    int K = p->K, r = (K - 1) / 2;
+    double s = 0.0;
+    for (int pp = 0; pp < K; ++pp)
+        for (int qq = 0; qq < K; ++qq) {
+            int ii = wrap(i + pp - r, p->H), jj = wrap(j + qq - r, p->W);
+            s += b[((size_t)c * K + pp) * K + qq] * orc_conv_at(p, b, v, c, ii, jj);
+        }
+    double xc = at(p, x, c, i, j), vc = at(p, v, c, i, j);
+    double hJ = orc_ddphi(p, xc - at(p, x, c, i, j - 1)) * (vc - at(p, v, c, i, j - 1)) -
+                orc_ddphi(p, at(p, x, c, i, j + 1) - xc) * (at(p, v, c, i, j + 1) - vc) +
+                orc_ddphi(p, xc - at(p, x, c, i - 1, j)) * (vc - at(p, v, c, i - 1, j)) -
+                orc_ddphi(p, at(p, x, c, i + 1, j) - xc) * (at(p, v, c, i + 1, j) - vc);
+    return s + p->alpha * hJ;
+}
+
 /* Lipschitz constant of grad_x h on channel c: ||B_c||^2 <= ||b_c||_1^2
  * (Young), plus alpha ||D||^2 sup phi'' with ||D||^2 = 8 in 2D. */
 double orc_lipschitz(const orc_prob *p, const double *b, int c)

@@ -29,7 +29,8 @@ EXPORTS = ("adp_problem_create", "adp_problem_destroy", "adp_apply_B", "adp_appl
            "adp_grad_lower", "adp_hess_vec", "adp_lower_solve", "adp_upper_loss", "adp_hypergrad",
            "adp_cross_t", "adp_maid_init", "adp_maid_step", "adp_conv_passes_last",
            "adp_grid_size", "adp_warps_per_cta", "adp_last_kernel_ms", "adp_trace_enable",
-           "adp_trace_read", "adp_lower_solve_noalloc", "adp_last_error", "adp_status_string")
+           "adp_trace_read", "adp_lower_solve_noalloc", "adp_selftest_wait_timeout", "adp_last_error",
+           "adp_status_string")
 
 
 class AdpError(RuntimeError):
@@ -92,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
             "adp_trace_enable": (i, [P, i]),
             "adp_trace_read": (i, [P, ct.POINTER(ct.c_longlong), i]),
             "adp_lower_solve_noalloc": (i, [ct.POINTER(adp_params), vp, vp, vp, d, i, vp, ip, dp]),
+            "adp_selftest_wait_timeout": (i, [P]),
             "adp_last_error": (ct.c_char_p, []),
             "adp_status_string": (ct.c_char_p, [i]),
         }
@@ -279,6 +281,11 @@ class Problem:
 
     def last_kernel_ms(self) -> float:
         return float(self.lib.adp_last_kernel_ms(self.handle))
+
+    def selftest_wait_timeout(self) -> int:
+        """Run the failure-path diagnostic (a grid barrier CTA 0 never reaches);
+        returns the raw status, ADP_ETIMEOUT when the bounded waits work."""
+        return int(self.lib.adp_selftest_wait_timeout(self.handle))
 
     def trace_enable(self, cap: int):
         _check(self.lib.adp_trace_enable(self.handle, int(cap)))

@@ -393,6 +393,14 @@ adp_status adp_maid_step(adp_problem *p, adp_maid_state *s, void *b, void *x, vo
     return (o->accepted || o->stopped) ? ADP_OK : ADP_ELSFAIL;
 }
 
+adp_status adp_selftest_wait_timeout(adp_problem *p)
+{
+    if (!p) return set_err(ADP_EINVAL, "null problem%s", "", 0);
+    if (p->grid < 2) return set_err(ADP_EINVAL, "the self-test needs a launch of at least 2 CTAs (this problem has %s%lld)", "", p->grid);
+    return dispatch_job(p, M_WAIT_SELFTEST, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0,
+                        nullptr);
+}
+
 long long adp_conv_passes_last(adp_problem *p) { return p ? p->hout->conv_passes : -1; }
 int adp_grid_size(adp_problem *p) { return p ? p->grid : -1; }
 int adp_warps_per_cta(adp_problem *p) { return p ? p->nw : -1; }

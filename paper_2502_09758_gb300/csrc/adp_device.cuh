@@ -440,7 +440,7 @@ __device__ __forceinline__ T ddphi(int reg, T t, T g, T ig)
 
 enum Mode : int {
     M_APPLY_B = 0, M_APPLY_BT, M_GRAD_LOWER, M_HESS_VEC, M_LOWER_SOLVE, M_UPPER_LOSS,
-    M_HYPERGRAD, M_CROSS, M_MAID
+    M_HYPERGRAD, M_CROSS, M_MAID, M_WAIT_SELFTEST
 };
 
 struct MaidIn {

@@ -868,6 +868,11 @@ __global__ void __launch_bounds__(MAXNW * 32, 1) adp_kernel(const __grid_constan
     }
     case M_CROSS: e.cross(jb.b, jb.x, jb.v, jb.z, false, false, passes); break;
     case M_MAID: e.maid(jb); break;
+    case M_WAIT_SELFTEST:
+        // diagnostic: CTA 0 never arrives, so every other CTA's bounded wait at
+        // this barrier runs out and records ST_TIMEOUT
+        if (blockIdx.x != 0) e.sync();
+        break;
     default: break;
     }
     if (lead) cx.out->barriers = (int)e.epoch;

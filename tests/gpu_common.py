@@ -43,7 +43,7 @@ class Pair:
 
     @staticmethod
     def n(t):
-        return t.double().cpu().numpy()
+        return t.detach().double().cpu().numpy()
 
 
 def rel(a, b):

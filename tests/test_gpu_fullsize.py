@@ -1,0 +1,131 @@
+"""Parity at the full sizes of the large workloads (512 x 512 RGB with K = 31;
+2048 x 2048 RGB with K = 63), in the launch configuration the library picks
+for them, on outputs sampled where the oracle can compute them one by one
+(edges and corners included), and through identities that hold at any size.
+
+Tolerance for a sampled operator output in FP32: relative L2 over the samples
+<= max(1e-6, 2 K u), u = 2^-24.  Both sides see the same FP32-rounded inputs;
+the GPU accumulates the K^2 products of an output in FP32, whose rounding
+errors grow like the square root of the number of terms (K), times a safety
+factor of 2.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2502_09758_gb300 import adp, synth
+from gpu_common import Pair, need_gpu, rel
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+_CACHE = {}
+
+
+def pair_for(name):
+    if name not in _CACHE:
+        inst = synth.rgb512_k31(0) if name == "rgb512_k31" else synth.rgb2048_k63(0)
+        _CACHE[name] = Pair(inst, prec=adp.ADP_F32)
+    return _CACHE[name]
+
+
+def sample_idx(C, H, W, n, seed):
+    rng = np.random.default_rng(seed)
+    idx = [(c, i, j) for c in range(C) for i in (0, H - 1) for j in (0, W - 1)]   # corners
+    idx += [(int(rng.integers(C)), int(rng.integers(H)), int(rng.integers(W))) for _ in range(n)]
+    idx += [(0, 0, int(rng.integers(W))), (C - 1, H - 1, int(rng.integers(W))),
+            (0, int(rng.integers(H)), 0), (C - 1, int(rng.integers(H)), W - 1)]            # edges
+    return idx
+
+
+def take(img, idx):
+    return np.array([img[c, i, j] for c, i, j in idx])
+
+
+NAMES = ["rgb512_k31", "rgb2048_k63"]
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_operators_sampled(name):
+    pr = pair_for(name)
+    C, H, W = pr.inst.shape
+    K = pr.inst.K
+    tol = max(1e-6, 2 * K * U32)
+    x = pr.rounded(pr.inst.x_true)
+    b = pr.rounded(pr.inst.b_true)
+    idx = sample_idx(C, H, W, 200, 1)
+    out = pr.n(pr.prob.apply_B(pr.t(b), pr.t(x)))
+    assert rel(take(out, idx), pr.P.conv_at(b, x, idx)) <= tol
+    outT = pr.n(pr.prob.apply_Bt(pr.t(b), pr.t(x)))
+    assert rel(take(outT, idx), pr.P.conv_adj_at(b, x, idx)) <= tol
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_gradient_and_hessian_sampled(name):
+    pr = pair_for(name)
+    C, H, W = pr.inst.shape
+    K = pr.inst.K
+    tol = max(2e-6, 4 * K * U32)
+    x = pr.y
+    b = pr.a
+    idx = sample_idx(C, H, W, 12 if K > 40 else 40, 2)
+    g = pr.n(pr.prob.grad_lower(pr.t(b), pr.t(x))[0])
+    assert rel(take(g, idx), pr.P.grad_h_at(b, x, pr.y, idx)) <= tol * 10   # B^T of a cancelling residual
+    rng = np.random.default_rng(5)
+    v = pr.rounded(rng.standard_normal((C, H, W)))
+    hv = pr.n(pr.prob.hess_vec(pr.t(b), pr.t(x), pr.t(v)))
+    assert rel(take(hv, idx), pr.P.hess_h_vec_at(b, x, v, idx)) <= tol
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_first_fista_update_sampled(name):
+    """One FISTA update from x0 = y: x1 = y - tau_c grad_x h(y) with
+    tau_c = 1/(||b_c||_1^2 + 8 alpha sup phi''); theta_1 = 0, so the solve
+    returns x1."""
+    pr = pair_for(name)
+    C, H, W = pr.inst.shape
+    K = pr.inst.K
+    b = pr.a
+    xg = pr.t(pr.y)
+    it, _, _ = pr.prob.lower_solve(pr.t(b), xg, 0.0, 1)
+    assert it == 1
+    idx = sample_idx(C, H, W, 12 if K > 40 else 40, 3)
+    tau = np.array([1.0 / pr.P.lipschitz(b, c) for c in range(C)])
+    g = pr.P.grad_h_at(b, pr.y, pr.y, idx)
+    x1 = np.array([pr.y[c, i, j] for c, i, j in idx]) - tau[[c for c, _, _ in idx]] * g
+    assert rel(take(pr.n(xg), idx), x1) <= 1e-6
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_cross_term_identity(name):
+    """The kernel-gradient correlation is the adjoint of b -> d/db grad_x h:
+    <cross(x, v), d> = <D v, B x - y> + <B v, D x> for any kernel d (D the
+    convolution by d), evaluated with the library's own (sample-checked)
+    operator; holds at any size."""
+    pr = pair_for(name)
+    C, H, W = pr.inst.shape
+    K = pr.inst.K
+    rng = np.random.default_rng(9)
+    b = pr.t(pr.a)
+    x = pr.t(pr.y)
+    v = pr.t(pr.rounded(rng.standard_normal((C, H, W)) * 0.1))
+    d = pr.t(pr.rounded(rng.standard_normal((C, K, K))))
+    z = pr.prob.cross_t(b, x, v).double()
+    lhs = float((z * d.double()).sum())
+    res = pr.prob.apply_B(b, x).double() - pr.t(pr.y).double()
+    rhs = float((pr.prob.apply_B(d, v).double() * res).sum() +
+                (pr.prob.apply_B(b, v).double() * pr.prob.apply_B(d, x).double()).sum())
+    assert abs(lhs - rhs) <= 1e-4 * max(abs(rhs), 1e-30), (lhs, rhs)
+
+
+def test_free_large_problems():
+    for p in _CACHE.values():
+        p.prob.close()
+    _CACHE.clear()
+    torch.cuda.empty_cache()

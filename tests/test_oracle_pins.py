@@ -457,3 +457,23 @@ def test_maid_stop_rule_sec42(orc):
     assert not acc and s.stopped == 1 and s.rounds == 2          # 1e-2 -> 5e-3 -> 2.5e-3
     assert s.eps == pytest.approx(2.5e-3) and s.trials == 2 + 3
     np.testing.assert_array_equal(b, inst.a)
+
+
+# ------------------------------------------------------------ single outputs
+@pytest.mark.parametrize("reg,par", [(oracle.REG_HUBER, 0.05), (oracle.REG_SQRT, 0.1), (oracle.REG_QUAD, 1.0)])
+def test_single_output_functions_match_whole_image(orc, reg, par):
+    """The per-pixel evaluations used for sampled checks at large sizes agree
+    with the whole-image functions (themselves pinned above) at every pixel,
+    including the periodic wrap at all four edges and a kernel wider than the
+    image."""
+    for C, H, W, K in [(2, 9, 11, 5), (1, 6, 5, 7)]:
+        rng = np.random.default_rng(C * 100 + K)
+        P = oracle.Problem(C, H, W, K, alpha=0.3, reg=reg, reg_param=par)
+        b = rng.standard_normal((C, K, K))
+        x, y, v = (rng.standard_normal((C, H, W)) for _ in range(3))
+        idx = [(c, i, j) for c in range(C) for i in range(H) for j in range(W)]
+        np.testing.assert_allclose(P.conv_at(b, x, idx), P.conv(b, x).ravel(), rtol=0, atol=1e-13)
+        np.testing.assert_allclose(P.conv_adj_at(b, x, idx), P.conv_adj(b, x).ravel(), rtol=0, atol=1e-13)
+        np.testing.assert_allclose(P.grad_h_at(b, x, y, idx), P.grad_h(b, x, y).ravel(), rtol=0, atol=1e-11)
+        np.testing.assert_allclose(P.hess_h_vec_at(b, x, v, idx), P.hess_h_vec(b, x, v).ravel(), rtol=0,
+                                   atol=1e-11)
