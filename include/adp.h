@@ -180,18 +180,24 @@ double adp_last_kernel_ms(adp_problem *p);
  * (C x H x W), b (C x K x K) and x are the caller's device pointers, `stream`
  * a cudaStream_t, and the workspace is one fixed array in the library's
  * device memory, ADP_NOALLOC_SCRATCH_BYTES in size, which every GPU that
- * loads the library holds until the process exits.  Images are limited to
- * C*H*W*element size <= ADP_NOALLOC_MAX_IMAGE_BYTES (e.g. 3 x 512 x 512 in
- * FP32); larger ones are rejected with ADP_EINVAL.  The first call on a device
- * looks up the array's device address and sets kernel attributes for that
- * device (once per device, with it current); make that first call before any
- * stream capture.  All calls share the array and it keeps the last call's
- * contents (each call clears what must start at zero), so calls whose GPU work
- * overlaps -- on different streams, or from different threads -- race and
- * must be serialised by the caller.  Calls no cudaMalloc, cudaFree or other
- * allocating routine. */
-#define ADP_NOALLOC_MAX_IMAGE_BYTES 3276800
-#define ADP_NOALLOC_SCRATCH_BYTES (512 + 8 * 512 * 8 + 5 * ADP_NOALLOC_MAX_IMAGE_BYTES)
+ * loads the library holds until the process exits.  The solve keeps seven
+ * images in the padded layout of the library (periodic ghost borders of
+ * Gy = max(r, 1) rows and Gx = max(r rounded up to 4, 4) columns, rows padded
+ * to a multiple of 4 elements; r = (K-1)/2), each limited to
+ * C*(H+2Gy)*round_up(W+2Gx, 4)*element size <= ADP_NOALLOC_MAX_IMAGE_BYTES
+ * (e.g. 3 x 512 x 512 in FP32 with any K up to 63), and the kernel weights to
+ * 4*C*K*round_up(K, 16 in FP32 or 8 in FP64)*element size <=
+ * ADP_NOALLOC_WEIGHT_BYTES; larger problems are rejected with ADP_EINVAL.
+ * The first call on a device looks up the array's device address and sets
+ * kernel attributes for that device (once per device, with it current); make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents (each call clears what must start at
+ * zero), so calls whose GPU work overlaps -- on different streams, or from
+ * different threads -- race and must be serialised by the caller.  Calls no
+ * cudaMalloc, cudaFree or other allocating routine. */
+#define ADP_NOALLOC_MAX_IMAGE_BYTES 4194304
+#define ADP_NOALLOC_WEIGHT_BYTES 1048576
+#define ADP_NOALLOC_SCRATCH_BYTES (512 + 8 * 512 * 8 + ADP_NOALLOC_WEIGHT_BYTES + 7 * ADP_NOALLOC_MAX_IMAGE_BYTES)
 adp_status adp_lower_solve_noalloc(const adp_params *params, const void *y, const void *b, void *x, double eps,
                                    int max_iters, void *stream, int *iters, double *gradnorm);
 

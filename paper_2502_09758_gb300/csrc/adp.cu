@@ -18,6 +18,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <type_traits>
 
 using namespace adp;
@@ -52,36 +53,90 @@ struct adp_problem {
     int device, grid, nw;  // CTAs of the cooperative launch, warps per CTA
     size_t smem;           // dynamic shared memory per CTA (bytes)
     size_t esize;
-    void *y, *a;
-    void *img[12];         // X0 X1 Y0 Y1 U V G R P0 P1 HP XT
+    Geom g;                // padded layout and strips
+    void *ws;              // NBUF padded images
+    void *wg;              // two slots of both kernel orientations (global, read through L1)
+    void *a;
     void *BT, *ZK;
     double *part, *zpart;
     unsigned *bar;
     DevOut *dout, *hout;
     double *a_host;        // a in FP64 on the host (for L of grad g)
-    int MR, Kp, nx, ny, nstrips;
     long long *trace;      // optional barrier trace (2 * trace_cap values)
     int trace_cap;
+    CUtensorMap map_s, map_1, map_i;
     cudaEvent_t ev0, ev1;  // bracket the cooperative launch on the problem's stream
     float last_ms;
 };
+
+// ------------------------------------------------------------ tensor maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn(char *err, int errlen)
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)ptr;
+    });
+    if (!fn) snprintf(err, errlen, "cuTensorMapEncodeTiled is not available from the driver");
+    return fn;
+}
+
+namespace adp {
+int encode_tensor_maps(void *ws, int nbuf, int C, const Geom &g, int esize, int MR, int NX, CUtensorMap *map_s,
+                       CUtensorMap *map_1, CUtensorMap *map_i, char *err, int errlen)
+{
+    EncodeTiledFn fn = encode_fn(err, errlen);
+    if (!fn) return 1;
+    const CUtensorMapDataType dt = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    // [buffer][channel][padded row][padded column], innermost first
+    const cuuint64_t dims[4] = {(cuuint64_t)g.Wp, (cuuint64_t)g.Hp, (cuuint64_t)C, (cuuint64_t)nbuf};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.Wp * esize, (cuuint64_t)g.HWp * esize,
+                                   (cuuint64_t)g.Np * esize};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const cuuint32_t box_s[4] = {(cuuint32_t)g.BW, (cuuint32_t)NX, 1, 1};
+    const cuuint32_t box_1[4] = {40, (cuuint32_t)(MR + 2), 1, 1};
+    const cuuint32_t box_i[4] = {32, (cuuint32_t)MR, 1, 1};
+    struct { CUtensorMap *m; const cuuint32_t *box; const char *name; } maps[3] = {
+        {map_s, box_s, "stage"}, {map_1, box_1, "halo-1"}, {map_i, box_i, "interior"}};
+    for (auto &m : maps) {
+        const CUresult r = fn(m.m, dt, 4, ws, dims, strides, m.box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            snprintf(err, errlen, "tensor map encoding (%s box) failed with CUresult %d", m.name, (int)r);
+            return 1;
+        }
+    }
+    return 0;
+}
+} // namespace adp
 
 template <typename T>
 static Ctx<T> make_ctx(const adp_problem *p)
 {
     Ctx<T> c;
+    memset(&c, 0, sizeof c);
     const adp_params &q = p->prm;
-    c.C = q.C; c.H = q.H; c.W = q.W; c.K = q.K; c.r = (q.K - 1) / 2; c.Kp = p->Kp;
-    c.nx = p->nx; c.ny = p->ny; c.nstrips = p->nstrips;
-    c.PA = 32 + 2 * c.r; c.RA = p->MR + c.Kp - 1;
+    const Geom &g = p->g;
+    c.map_s = p->map_s; c.map_1 = p->map_1; c.map_i = p->map_i;
+    c.C = q.C; c.H = q.H; c.W = q.W; c.K = q.K; c.r = g.r; c.Kp = g.Kp;
+    c.r4 = g.r4; c.Gx = g.Gx; c.Gy = g.Gy; c.Wp = g.Wp; c.Hp = g.Hp; c.BW = g.BW;
+    c.nx = g.nx; c.ny = g.ny; c.nstrips = g.nstrips; c.wsm = g.wsm; c.multiwrap = g.multiwrap;
+    c.N = g.N; c.HW = g.HW; c.HWp = g.HWp; c.Np = g.Np;
     c.trace = p->trace; c.trace_cap = p->trace_cap;
-    c.HW = (long long)q.H * q.W; c.N = c.HW * q.C;
     c.reg = q.reg; c.alpha = q.alpha; c.rp = q.reg_param; c.beta = q.beta; c.w0 = q.sobolev_w0;
     c.ddphi_max = q.reg == ADP_REG_QUAD ? 1.0 : 1.0 / q.reg_param;
     c.alphaT = (T)q.alpha; c.rpT = (T)q.reg_param; c.irpT = (T)(1.0 / q.reg_param);
-    c.y = (const T *)p->y; c.a = (const T *)p->a;
-    T **im[12] = {&c.X0, &c.X1, &c.Y0, &c.Y1, &c.U, &c.V, &c.G, &c.R, &c.P0, &c.P1, &c.HP, &c.XT};
-    for (int i = 0; i < 12; ++i) *im[i] = (T *)p->img[i];
+    c.ws = (T *)p->ws; c.wg = (T *)p->wg; c.a = (const T *)p->a;
     c.BT = (T *)p->BT; c.ZK = (T *)p->ZK;
     c.part = p->part; c.zpart = p->zpart; c.bar = p->bar; c.out = p->dout;
     const double to = q.wait_timeout_s > 0 ? q.wait_timeout_s : 2.0;
@@ -155,9 +210,8 @@ void adp_problem_destroy(adp_problem *p)
     if (!p) return;
     cudaSetDevice(p->device);
     cudaStreamSynchronize(p->stream);
-    void *ptrs[] = {p->y, p->a, p->BT, p->ZK, p->part, p->zpart, p->bar, p->dout, p->trace};
+    void *ptrs[] = {p->ws, p->wg, p->a, p->BT, p->ZK, p->part, p->zpart, p->bar, p->dout, p->trace};
     for (void *q : ptrs) if (q) cudaFree(q);
-    for (void *q : p->img) if (q) cudaFree(q);
     if (p->hout) cudaFreeHost(p->hout);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
@@ -185,11 +239,10 @@ adp_status adp_problem_create(const adp_params *prm, const void *y, const void *
     p->prm = q;
     p->stream = (cudaStream_t)stream;
     p->esize = q.prec == ADP_F32 ? sizeof(float) : sizeof(double);
-    p->MR = q.prec == ADP_F32 ? Cfg<float>::MR : Cfg<double>::MR;
-    p->Kp = round_up(q.K, q.prec == ADP_F32 ? Cfg<float>::PC : Cfg<double>::PC);
-    p->nx = (q.W + 31) / 32;
-    p->ny = (q.H + p->MR - 1) / p->MR;
-    p->nstrips = q.C * p->nx * p->ny;
+    p->g = q.prec == ADP_F32 ? make_geom<float>(q.C, q.H, q.W, q.K) : make_geom<double>(q.C, q.H, q.W, q.K);
+    const Geom &g = p->g;
+    const int MR = q.prec == ADP_F32 ? Cfg<float>::MR : Cfg<double>::MR;
+    const int NX = q.prec == ADP_F32 ? Cfg<float>::PC + MR - 1 : Cfg<double>::PC + MR - 1;
 
     adp_status st = ADP_OK;
 #define CKC(call)                                                                            \
@@ -209,19 +262,17 @@ adp_status adp_problem_create(const adp_params *prm, const void *y, const void *
     CKC(cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
     // warps per CTA: as many as shared memory allows (the kernel's static shared
     // memory is below 5 KB; keep that margin)
-    int w_elems = 0, warp_elems = 0, total = 0;
-    int nw = MAXNW;
+    int nw = MAXNW, total = 0;
     for (; nw >= 1; --nw) {
-        if (q.prec == ADP_F32) smem_layout<float>(q.C, q.K, nw, w_elems, warp_elems, total);
-        else smem_layout<double>(q.C, q.K, nw, w_elems, warp_elems, total);
-        if ((size_t)total * p->esize + 5 * 1024 <= (size_t)maxsmem) break;
+        total = q.prec == ADP_F32 ? Layout<float>(q.C, q.K, nw, g.wsm).total : Layout<double>(q.C, q.K, nw, g.wsm).total;
+        if ((size_t)total * p->esize + 128 + 5 * 1024 <= (size_t)maxsmem) break;
     }
     if (nw < 1) {
         adp_problem_destroy(p);
         return set_err(ADP_EINVAL, "kernel too large for shared memory%s (K = %lld)", "", q.K);
     }
     p->nw = nw;
-    p->smem = (size_t)total * p->esize;
+    p->smem = (size_t)total * p->esize + 128;   // + alignment slack of the TMA destinations
     const void *kfn = q.prec == ADP_F32 ? kernel_f32() : kernel_f64();
     // opt in to the device's whole dynamic shared memory (less the static part)
     // rather than this problem's size: the attribute is shared by every problem
@@ -238,16 +289,17 @@ adp_status adp_problem_create(const adp_params *prm, const void *y, const void *
     // warp); beyond that add CTAs up to the co-residency limit
     const long long maxgrid = (long long)occ * nsm;
     long long grid;
-    if (p->nstrips <= (long long)nsm * nw) grid = p->nstrips < nsm ? p->nstrips : nsm;
-    else grid = ((long long)p->nstrips + nw - 1) / nw;
+    if (g.nstrips <= (long long)nsm * nw) grid = g.nstrips < nsm ? g.nstrips : nsm;
+    else grid = ((long long)g.nstrips + nw - 1) / nw;
     if (grid > maxgrid) grid = maxgrid;
     if (grid > GT_MAX) grid = GT_MAX;   // staging buffer of the grid totals
     p->grid = (int)grid;
 
-    const size_t N = (size_t)q.C * q.H * q.W, KK = (size_t)q.C * q.K * q.K;
-    CKC(cudaMalloc(&p->y, N * p->esize));
+    const size_t KK = (size_t)q.C * q.K * q.K;
+    const size_t wsbytes = (size_t)NBUF * g.Np * p->esize;
+    CKC(cudaMalloc(&p->ws, wsbytes));
+    CKC(cudaMalloc(&p->wg, (size_t)4 * q.C * q.K * g.Kp * p->esize));
     CKC(cudaMalloc(&p->a, KK * p->esize));
-    for (int i = 0; i < 12; ++i) CKC(cudaMalloc(&p->img[i], N * p->esize));
     CKC(cudaMalloc(&p->BT, KK * p->esize));
     CKC(cudaMalloc(&p->ZK, KK * p->esize));
     CKC(cudaMalloc((void **)&p->part, (size_t)NSLOT * p->grid * sizeof(double)));
@@ -257,9 +309,17 @@ adp_status adp_problem_create(const adp_params *prm, const void *y, const void *
     CKC(cudaMallocHost((void **)&p->hout, sizeof(DevOut)));
     CKC(cudaEventCreate(&p->ev0));
     CKC(cudaEventCreate(&p->ev1));
-    CKC(cudaMemcpyAsync(p->y, y, N * p->esize, cudaMemcpyDeviceToDevice, p->stream));
+    {
+        char emsg[200];
+        if (encode_tensor_maps(p->ws, NBUF, q.C, g, (int)p->esize, MR, NX, &p->map_s, &p->map_1, &p->map_i, emsg,
+                               sizeof emsg)) {
+            adp_problem_destroy(p);
+            record_error(emsg);
+            return ADP_ECUDA;
+        }
+    }
     CKC(cudaMemcpyAsync(p->a, a, KK * p->esize, cudaMemcpyDeviceToDevice, p->stream));
-    for (int i = 0; i < 12; ++i) CKC(cudaMemsetAsync(p->img[i], 0, N * p->esize, p->stream));
+    CKC(cudaMemsetAsync(p->ws, 0, wsbytes, p->stream));
     p->a_host = (double *)malloc(KK * sizeof(double));
     if (!p->a_host) { adp_problem_destroy(p); return set_err(ADP_ENOMEM, "host allocation failed%s", "", 0); }
     if (q.prec == ADP_F32) {
@@ -274,6 +334,12 @@ adp_status adp_problem_create(const adp_params *prm, const void *y, const void *
         CKC(cudaStreamSynchronize(p->stream));
     }
 #undef CKC
+    // y into its padded buffer (ghosts included); the caller may free y afterwards
+    st = dispatch_job(p, M_IMPORT_Y, nullptr, y, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, nullptr);
+    if (st != ADP_OK) {
+        adp_problem_destroy(p);
+        return st;
+    }
     *out = p;
     return ADP_OK;
 }

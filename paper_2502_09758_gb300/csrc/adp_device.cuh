@@ -4,6 +4,7 @@
 // host code in adp.cu.
 #pragma once
 
+#include <cuda.h>          // CUtensorMap (type only; encoded on the host through the runtime's entry point)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -315,60 +316,84 @@ __device__ __forceinline__ typename Scal<T>::S grid_total(const typename Scal<T>
     return *bcast;
 }
 
-// ------------------------------------------------------------ async copies
-__device__ __forceinline__ void cp_async(float *dst, const float *src)
+// ------------------------------------------------------------ TMA
+// Tiled bulk tensor copies (cp.async.bulk.tensor) into shared memory, with
+// completion counted in bytes on a per-warp mbarrier.  The workspace is one
+// 4D tensor [buffer][channel][padded row][padded column]; every tile the
+// engine needs is a box of it.  The innermost coordinate is always a multiple
+// of 4 elements (16 bytes).  Waits are bounded: after timeout_ns the waiter
+// reports failure and the caller unwinds.
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, unsigned count)
 {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(src) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ void cp_async(double *dst, const double *src)
+// makes the initialised barriers visible to the async proxy (TMA completions)
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, unsigned bytes)
 {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
 }
 
-__device__ __forceinline__ void cp_async_wait_all()
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, unsigned parity)
 {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(mbar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
 }
 
-// One warp stages rows x cols (cols <= 96) of the periodic image channel at
-// cbase into s (row pitch `pitch`): s[ii][jj] = src[wrap(r0+ii), wrap(c0+jj)].
-// Asynchronous; complete with cp_async_wait_all() and __syncwarp().
-template <typename T>
-__device__ __forceinline__ void warp_stage(T *s, int pitch, int rows, int cols, const T *src, long long cbase,
-                                           int r0, int c0, int H, int W, int lane)
+// bounded wait for the given phase parity of mbar; false when the budget ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, unsigned parity, long long timeout_ns)
 {
-    int gj[3];
-#pragma unroll
-    for (int u = 0; u < 3; ++u) gj[u] = wrapi(c0 + lane + 32 * u, W);
-    int gi = wrapi(r0, H);
-    for (int ii = 0; ii < rows; ++ii) {
-        const T *rowp = src + cbase + (long long)gi * W;
-#pragma unroll
-        for (int u = 0; u < 3; ++u) {
-            const int jj = lane + 32 * u;
-            if (jj < cols) cp_async(s + ii * pitch + jj, rowp + gj[u]);
-        }
-        if (++gi == H) gi = 0;
+    if (mbar_try_wait(mbar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        if (mbar_try_wait(mbar, parity)) return true;
+        if ((long long)(globaltimer_ns() - t0) > timeout_ns) return false;
     }
 }
 
-// Register-blocked direct correlation of one 1 x MR output column strip:
-//   acc[m] += sum_{q<K} sum_{p<Kq} wt[q*Kq + p] * s[(m + p)*pitch + lj + q]
-// with the kernel stored column-major (wt[q][p], p contiguous) and its rows
-// zero-padded to Kq, a multiple of PC.  The work is cut into chunks of PC
-// kernel rows of one kernel column; a chunk needs PC + MR - 1 values of the
-// thread's tile column and PC weights (vector loads, broadcast to the warp),
-// which are loaded into registers one chunk ahead of the MR x PC FMAs that use
-// them, so shared-memory latency overlaps arithmetic.
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int w,
+                                            uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::
+            "r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(mbar))
+        : "memory");
+}
+
+// Proxy fences.  Global: orders generic-proxy writes before later async-proxy
+// (TMA) reads of them; taken by every writer before a grid barrier and by the
+// issuing lane after it.  Shared: orders a lane's generic reads and writes of a
+// staging buffer before the TMA that refills it.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Register-blocked direct correlation of one 32-column x MR-row strip over
+// one stage: PC consecutive kernel rows p0 .. p0+PC-1, all K kernel columns.
+//   acc[m] += sum_{q<K} sum_{p<PC} w[q*Kp + p] * s[(m + p)*pitch + lj + q]
+// s holds the PC + MR - 1 tile rows of the stage; w points at row p0 of a
+// kernel stored column-major (w[q][p], p contiguous, rows zero-padded to Kp).
+// Per kernel column the thread needs PC + MR - 1 values of its tile column and
+// PC weights (vector loads, the same address in every lane); they are loaded
+// one column ahead of the MR x PC FMAs that use them, so load latency
+// overlaps arithmetic.  The weights come through a generic pointer: shared
+// memory, or global memory read through L1 (coherent after the grid barrier
+// that follows their writing).
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using V = float4; static constexpr int L = 4; };
 template <> struct Vec4<double> { using V = double2; static constexpr int L = 2; };
 
 template <typename T, int PC>
-__device__ __forceinline__ void load_wchunk(const T *__restrict__ wq, T (&wv)[PC])
+__device__ __forceinline__ void load_wchunk(const T *wq, T (&wv)[PC])
 {
     using V = typename Vec4<T>::V;
     constexpr int L = Vec4<T>::L;
@@ -382,19 +407,18 @@ __device__ __forceinline__ void load_wchunk(const T *__restrict__ wq, T (&wv)[PC
 }
 
 template <typename T, int MR, int PC>
-__device__ __forceinline__ void corr_strip(const T *__restrict__ s, int pitch, const T *__restrict__ wt,
-                                           int K, int Kq, int lj, T (&acc)[MR])
+__device__ __forceinline__ void corr_stage(const T *__restrict__ s, int pitch, const T *w, int K,
+                                           int Kp, int lj, T (&acc)[MR])
 {
     constexpr int NX = PC + MR - 1;
     T xa[NX], wa[PC], xb[NX], wb[PC];
-    int q = 0, p0 = 0;
+    int q = 0;
     auto load = [&](T (&xv)[NX], T (&wv)[PC]) {
-        const T *col = s + p0 * pitch + lj + q;
+        const T *col = s + lj + q;
 #pragma unroll
         for (int i = 0; i < NX; ++i) xv[i] = col[i * pitch];
-        load_wchunk<T, PC>(wt + q * Kq + p0, wv);
-        p0 += PC;
-        if (p0 == Kq) { p0 = 0; ++q; }
+        load_wchunk<T, PC>(w + q * Kp, wv);
+        ++q;
     };
     auto comp = [&](const T (&xv)[NX], const T (&wv)[PC]) {
 #pragma unroll
@@ -402,16 +426,15 @@ __device__ __forceinline__ void corr_strip(const T *__restrict__ s, int pitch, c
 #pragma unroll
             for (int m = 0; m < MR; ++m) acc[m] = fma(wv[p], xv[m + p], acc[m]);
     };
-    const int total = K * (Kq / PC);
     load(xa, wa);
-    int ci = 0;
-    for (; ci + 2 <= total; ci += 2) {
+    int qi = 0;
+    for (; qi + 2 <= K; qi += 2) {
         load(xb, wb);
         comp(xa, wa);
-        if (ci + 2 < total) load(xa, wa);
+        if (qi + 2 < K) load(xa, wa);
         comp(xb, wb);
     }
-    if (ci < total) comp(xa, wa);
+    if (qi < K) comp(xa, wa);
 }
 
 // phi' and phi'' of the regularisers (reg: 0 Huber, 1 sqrt, 2 quadratic);
@@ -440,7 +463,7 @@ __device__ __forceinline__ T ddphi(int reg, T t, T g, T ig)
 
 enum Mode : int {
     M_APPLY_B = 0, M_APPLY_BT, M_GRAD_LOWER, M_HESS_VEC, M_LOWER_SOLVE, M_UPPER_LOSS,
-    M_HYPERGRAD, M_CROSS, M_MAID, M_WAIT_SELFTEST
+    M_HYPERGRAD, M_CROSS, M_MAID, M_IMPORT_Y, M_WAIT_SELFTEST
 };
 
 struct MaidIn {
@@ -448,23 +471,52 @@ struct MaidIn {
     int max_bt, max_rounds, ll_max_iters, cg_max_iters, k;
 };
 
+// Workspace buffers: one padded image each (see Ctx).  The first NBUF_LOWER
+// are all a lower-level solve touches (the allocation-free entry holds only
+// those).
+enum Buf : int {
+    B_Y = 0,            // the data y^delta
+    B_X0, B_X1,         // FISTA x_k, x_{k+1}
+    B_Y0, B_Y1,         // FISTA y_k, y_{k+1}
+    B_U,                // residual B x - y, or B p in CG
+    B_XK,               // lower-level solution x~
+    NBUF_LOWER,
+    B_V = NBUF_LOWER,   // A x - y, or B x - y in the kernel gradient
+    B_G,                // grad g
+    B_R, B_P0, B_P1, B_HP, B_Q,   // CG
+    B_XT,               // backtracking trial solution
+    B_IN1,              // an imported input image
+    NBUF
+};
+
+// Launch record of one problem.  Images live in a padded layout: channel c,
+// row i, column j of buffer b sit at ws[((b*C + c)*Hp + i + Gy)*Wp + j + Gx],
+// and the Gy rows / Gx columns around each image hold its periodic copies
+// (ghosts), kept current by every writer.  Any strip's halo tile is then one
+// TMA box.  Gx is a multiple of 4 (16-byte aligned boxes) and at least the
+// halo width in columns, Gy the halo width in rows.
 template <typename T>
 struct Ctx {
-    int C, H, W, K, r, Kp;         // Kp: kernel rows padded to a multiple of the chunk PC
-    int nx, ny, nstrips;           // strips: nx per row band, ny bands per channel
-    int PA, RA;                    // halo-r tile pitch (32 + 2r) and rows (MR + Kp - 1)
-    long long *trace;              // optional: barrier timestamps of CTA 0 (arrive, leave)
+    CUtensorMap map_s, map_1, map_i;   // boxes: stage (BW x NX), halo-1 tile (40 x MR+2), interior (32 x MR)
+    int C, H, W, K, r, Kp;             // Kp: kernel rows padded to a multiple of the stage height PC
+    int r4, Gx, Gy, Wp, Hp;            // halo column origin step, ghost widths, padded sizes
+    int BW;                            // stage box width: columns col0 - r4 .. col0 - r4 + BW - 1
+    int nx, ny, nstrips;               // strips: nx per row band, ny bands per channel
+    int wsm;                           // 1: kernel weights in shared memory, 0: in wg (read through L1)
+    int multiwrap;                     // 1 when Gx > W or Gy > H (ghosts hold several periods)
+    long long N, HW, HWp, Np;          // dense and padded sizes (Np = C*Hp*Wp per buffer)
+    long long *trace;                  // optional: barrier timestamps of CTA 0 (arrive, leave)
     int trace_cap;
-    T alphaT, rpT, irpT;           // alpha, the regulariser parameter and its reciprocal (element type)
-    long long N, HW;
     int reg;
     double alpha, rp, beta, w0, ddphi_max;
-    const T *y, *a;                // data and the kernel of A (library copies)
-    T *X0, *X1, *Y0, *Y1, *U, *V, *G, *R, *P0, *P1, *HP, *XT;   // images
-    T *BT, *ZK;                    // kernels
-    double *part;                  // NSLOT x grid
-    double *zpart;                 // (grid * warps) x C*K*K
-    unsigned *bar;                 // barrier arrival counter
+    T alphaT, rpT, irpT;               // alpha, the regulariser parameter and its reciprocal
+    T *ws;                             // padded images (NBUF, or NBUF_LOWER for the lower solve alone)
+    T *wg;                             // two slots of both kernel orientations, 2 x 2 x C x K x Kp
+    const T *a;                        // kernel of A (library copy)
+    T *BT, *ZK;                        // kernels
+    double *part;                      // NSLOT x grid
+    double *zpart;                     // (grid * warps) x C*K*K
+    unsigned *bar;                     // barrier arrival counter
     DevOut *out;
     long long timeout_ns;
 };
@@ -473,28 +525,82 @@ template <typename T>
 struct Job {
     int mode;
     const T *b;       // kernel used by the operator
-    const T *x;       // image input
-    T *xo;            // image output
-    const T *v;       // second image input (Hessian direction, rhs, or q)
-    T *q;             // CG iterate in/out
+    const T *x;       // image input (dense, caller's)
+    T *xo;            // image output (dense, caller's)
+    const T *v;       // second image input (Hessian direction, rhs, or q) (dense)
+    T *q;             // CG iterate in/out (dense)
     T *z;             // kernel output
     T *bio;           // MAID: kernel in/out
+    const T *y;       // data to import first (allocation-free lower solve), or null
     double eps, delta;
     int max_iters, flag;
     MaidIn maid;
 };
 
-// Shared-memory footprint (elements of T) of one CTA with nw warps.
+// Shared-memory footprint (elements of T) of one CTA with nw warps: both
+// kernel orientations when wsm, then per warp two stage buffers (NX = PC + MR
+// - 1 rows x BW columns), two halo-1 tiles (MR+2 rows x 40), an interior tile
+// (MR x 32) and two mbarriers, each region starting on a 32-element boundary
+// (TMA destinations).
 template <typename T>
-__host__ __device__ inline void smem_layout(int C, int K, int nw, int &w_elems, int &warp_elems, int &total)
+struct Layout {
+    int r, r4, Kp, BW, NX, stage, tile1, tileI, w_elems, warp_elems, total;
+    __host__ __device__ Layout(int C, int K, int nw, int wsm)
+    {
+        constexpr int MR = Cfg<T>::MR, PC = Cfg<T>::PC;
+        r = (K - 1) / 2;
+        r4 = round_up(r, 4);
+        Kp = round_up(K, PC);
+        BW = round_up(32 + r + r4, 4);
+        NX = PC + MR - 1;
+        stage = round_up(NX * BW, 32);
+        tile1 = round_up((MR + 2) * 40, 32);
+        tileI = round_up(MR * 32, 32);
+        w_elems = wsm ? round_up(2 * C * Kp * K, 32) : 0;
+        warp_elems = 2 * stage + 2 * tile1 + tileI + 32;
+        total = w_elems + nw * warp_elems;
+    }
+};
+
+// Bytes of both kernel orientations kept in shared memory at most; larger
+// kernels stay in global memory so that shared memory holds eight warps' stages.
+constexpr int WSMEM_MAX_BYTES = 40 * 1024;
+
+// Geometry of a problem's padded layout and strips (host and device agree).
+struct Geom {
+    int r, r4, Gx, Gy, Wp, Hp, Kp, BW, nx, ny, nstrips, wsm, multiwrap;
+    long long HW, HWp, N, Np;
+};
+
+template <typename T>
+inline Geom make_geom(int C, int H, int W, int K)
 {
-    constexpr int MR = Cfg<T>::MR;
-    const int r = (K - 1) / 2, Kp = round_up(K, Cfg<T>::PC);
-    const int PA = 32 + 2 * r, RA = MR + Kp - 1;
-    w_elems = round_up(2 * C * Kp * K, 4);                   // flipped and as-stored kernels
-    // two halo-r tiles, two halo-1 tiles, one interior tile of epilogue operands
-    warp_elems = round_up(2 * RA * PA + 2 * (MR + 2) * 34 + MR * 32, 4);
-    total = w_elems + nw * warp_elems;
+    constexpr int MR = Cfg<T>::MR, PC = Cfg<T>::PC;
+    Geom g;
+    g.r = (K - 1) / 2;
+    g.r4 = round_up(g.r, 4);
+    g.Gx = g.r4 > 4 ? g.r4 : 4;
+    g.Gy = g.r > 1 ? g.r : 1;
+    g.Wp = round_up(W + 2 * g.Gx, 4);
+    g.Hp = H + 2 * g.Gy;
+    g.Kp = round_up(K, PC);
+    g.BW = round_up(32 + g.r + g.r4, 4);
+    g.nx = (W + 31) / 32;
+    g.ny = (H + MR - 1) / MR;
+    g.nstrips = C * g.nx * g.ny;
+    g.wsm = (long long)2 * C * K * g.Kp * (long long)sizeof(T) <= WSMEM_MAX_BYTES ? 1 : 0;
+    g.multiwrap = (g.Gx > W || g.Gy > H) ? 1 : 0;
+    g.HW = (long long)H * W;
+    g.HWp = (long long)g.Hp * g.Wp;
+    g.N = g.HW * C;
+    g.Np = g.HWp * C;
+    return g;
 }
+
+// Encodes the three tensor maps of a padded workspace of nbuf images (host
+// side, through the driver's cuTensorMapEncodeTiled); 0 on success.
+int encode_tensor_maps(void *ws, int nbuf, int C, const Geom &g, int esize, int MR, int NX, CUtensorMap *map_s,
+                       CUtensorMap *map_1, CUtensorMap *map_i, char *err, int errlen);
+
 
 } // namespace adp

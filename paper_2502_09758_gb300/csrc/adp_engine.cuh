@@ -2,16 +2,33 @@
 // member function and the cooperative kernel that runs one program of phases.
 // Included by the per-precision translation units adp_f32.cu and adp_f64.cu.
 //
+// Data: the images of a call live in one padded workspace (see Ctx).  Periodic
+// ghost rows and columns around each image are written together with the
+// pixels they copy, so every tile a strip needs is a rectangular box that one
+// TMA instruction (cp.async.bulk.tensor) stages into shared memory.  The
+// caller's dense buffers are imported at the start of a call and exported at
+// its end.
+//
 // Work decomposition: a strip is 32 columns x MR rows of one channel.  Strips
 // are dealt to warps warp-major (strip s goes to warp s mod (grid * warps) in
-// the order warp*grid + cta, so consecutive strips land on different SMs).  A
-// warp stages its strip's input with a periodic halo into its own shared
-// memory tiles with cp.async, then runs the register-blocked correlation.
+// the order warp*grid + cta, so consecutive strips land on different SMs).  The
+// correlation input of a strip is staged in stages of NX = PC + MR - 1 tile
+// rows (the rows that PC kernel rows need), double-buffered per warp: lane 0
+// issues stage k+1 on the warp's other mbarrier while the warp computes stage k.
 //
 // Convolution geometry (Eq. 2.4): (B x)[c,i,j] = sum_{p,q} b[c,p,q] x[c,i-p+r,j-q+r].
 // With the tile origin at (row0-r, col0-r), B x is the correlation of the tile
 // with the flipped kernel and B^T z the correlation with b as stored; both
-// orientations are kept in shared memory, rows zero-padded to Kp.
+// orientations are kept (rows zero-padded to Kp), in shared memory when they
+// fit beside the warps' stages, else in a global slot read through L1.  Stage boxes start at column col0 - r4
+// (r4 = r rounded up to 4, for 16-byte aligned boxes), so the correlation reads
+// a stage from column offset r4 - r.
+//
+// Failure handling: a grid barrier that gives up returns false in every
+// thread of its CTA (alive), and the programs unwind.  An mbarrier wait that
+// gives up raises ST_TIMEOUT and stops that warp's TMA work for the rest of the
+// launch (tmafail); the next grid barrier then fails everywhere.  Before the
+// kernel returns, such a warp waits (bounded) for its copies in flight.
 #pragma once
 
 #include "adp_device.cuh"
@@ -23,22 +40,31 @@ struct Eng {
     using Sc = Scal<T>;
     using S = typename Sc::S;      // reduction / control scalar (float-float or double)
     static constexpr int MR = Cfg<T>::MR;
-    static constexpr int EWB = 8;  // element-wise phases: loads issued per batch per thread
+    static constexpr int PC = Cfg<T>::PC;
+    static constexpr int NX = PC + MR - 1;
+    static constexpr int EWB = 4;  // element-wise phases: loads issued per batch per thread
     const Ctx<T> &cx;
-    T *wF, *wT;                    // CTA: flipped / as-stored kernels, C x K x Kp (column-major)
-    T *hA, *hB, *t1, *t2;          // this warp's tiles: two halo-r, two halo-1 (pitch 34)
+    const T *wF, *wT;              // kernel orientations in use (shared memory or a global slot)
+    T *wsm;                        // shared-memory home of both orientations (when cx.wsm)
+    T *sb0, *sb1;                  // this warp's two stage buffers (NX x BW)
+    T *t1, *t2;                    // this warp's halo-1 tiles (MR+2 x 40) (interior tiles in the kernel gradient)
     T *tF;                         // this warp's MR x 32 tile of per-pixel epilogue operands
+    uint64_t *mbar;                // this warp's two TMA completion barriers
+    unsigned mph;                  // bit i: parity of mbar[i]'s next completion
+    int wslot;                     // global weight slot written last
     S *red, *bcast, *gbuf;
     double *redd;                  // FP64 CTA reductions of small control quantities
     T *tau;                        // per-channel FISTA step 1/L_c
     int *sflag;
-    int lane, warp, tid, nw, gw, TW;
+    int lane, warp, tid, nw, gw, TW, off, ns;
     unsigned epoch;                // barriers passed so far (same in every thread)
-    bool alive;                    // false once a barrier gave up or a status was raised
+    bool alive;                    // false once a grid barrier failed (uniform in the CTA)
+    bool tmafail;                  // this warp gave up waiting for a TMA copy
 
     __device__ Eng(const Ctx<T> &c, unsigned char *smem, S *red_, S *bcast_, double *redd_, T *tau_, S *gbuf_,
                    int *sflag_)
-        : cx(c), red(red_), bcast(bcast_), gbuf(gbuf_), redd(redd_), tau(tau_), sflag(sflag_), epoch(0), alive(true)
+        : cx(c), mph(0), wslot(1), red(red_), bcast(bcast_), gbuf(gbuf_), redd(redd_), tau(tau_), sflag(sflag_),
+          epoch(0), alive(true), tmafail(false)
     {
         lane = threadIdx.x & 31;
         warp = threadIdx.x >> 5;
@@ -46,21 +72,32 @@ struct Eng {
         nw = blockDim.x >> 5;
         gw = warp * gridDim.x + blockIdx.x;
         TW = gridDim.x * nw;
-        int w_elems, warp_elems, total;
-        smem_layout<T>(cx.C, cx.K, nw, w_elems, warp_elems, total);
-        T *base = reinterpret_cast<T *>(smem);
-        wF = base;
-        wT = base + cx.C * cx.Kp * cx.K;
-        hA = base + w_elems + warp * warp_elems;
-        hB = hA + cx.RA * cx.PA;
-        t1 = hB + cx.RA * cx.PA;
-        t2 = t1 + (MR + 2) * 34;
-        tF = t2 + (MR + 2) * 34;
+        const Layout<T> L(cx.C, cx.K, nw, cx.wsm);
+        // TMA destinations: 128-byte aligned (the host adds 128 bytes of slack)
+        T *base = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem) + 127) & ~(uintptr_t)127);
+        wF = wT = nullptr;
+        wsm = base;
+        sb0 = base + L.w_elems + warp * L.warp_elems;
+        sb1 = sb0 + L.stage;
+        t1 = sb1 + L.stage;
+        t2 = t1 + L.tile1;
+        tF = t2 + L.tile1;
+        mbar = reinterpret_cast<uint64_t *>(tF + L.tileI);
+        off = cx.r4 - cx.r;
+        ns = cx.Kp / PC;
+        if (lane == 0) {
+            mbar_init(&mbar[0], 1);
+            mbar_init(&mbar[1], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
     }
 
+    // ------------------------------------------------------------ plumbing
     __device__ bool sync()
     {
         if (!alive) return false;
+        fence_proxy_async();           // this thread's global writes, for TMA reads after the barrier
         ++epoch;
         const bool tr = cx.trace && blockIdx.x == 0 && tid == 0 && (int)epoch <= cx.trace_cap;
         if (tr) cx.trace[2 * (epoch - 1)] = (long long)globaltimer_ns();
@@ -69,14 +106,47 @@ struct Eng {
         return alive;
     }
 
-    __device__ void fail(int st)
-    {
-        if (tid == 0) atomicCAS(&cx.out->status, ST_OK, st);
-        alive = false;
-    }
+    // record a failure status (first one wins); callers unwind uniformly
+    __device__ void raise(int st) const { atomicCAS(&cx.out->status, ST_OK, st); }
 
     __device__ long long gstride() const { return (long long)gridDim.x * blockDim.x; }
     __device__ long long gstart() const { return (long long)blockIdx.x * blockDim.x + tid; }
+
+    __device__ T *buf(int b) const { return cx.ws + (long long)b * cx.Np; }
+    // offset of pixel (c, i, j) inside a buffer
+    __device__ long long pidx(int c, int i, int j) const
+    {
+        return (long long)c * cx.HWp + (long long)(i + cx.Gy) * cx.Wp + (j + cx.Gx);
+    }
+
+    // write pixel (c, i, j) of buffer B and its periodic copies in the ghosts
+    __device__ void put(T *B, int c, int i, int j, T v) const
+    {
+        if (cx.multiwrap) {            // ghosts wider than the image: every copy in range
+            const long long cb = (long long)c * cx.HWp;
+            for (int ii = i - ((i + cx.Gy) / cx.H) * cx.H; ii < cx.H + cx.Gy; ii += cx.H)
+                for (int jj = j - ((j + cx.Gx) / cx.W) * cx.W; jj < cx.W + cx.Gx; jj += cx.W)
+                    B[cb + (long long)(ii + cx.Gy) * cx.Wp + (jj + cx.Gx)] = v;
+            return;
+        }
+        const long long o = pidx(c, i, j);
+        B[o] = v;
+        const bool xl = j < cx.Gx, xh = j >= cx.W - cx.Gx;
+        const bool yl = i < cx.Gy, yh = i >= cx.H - cx.Gy;
+        const long long dx = cx.W, dy = (long long)cx.H * cx.Wp;
+        if (xl) B[o + dx] = v;
+        if (xh) B[o - dx] = v;
+        if (yl) {
+            B[o + dy] = v;
+            if (xl) B[o + dy + dx] = v;
+            if (xh) B[o + dy - dx] = v;
+        }
+        if (yh) {
+            B[o - dy] = v;
+            if (xl) B[o - dy + dx] = v;
+            if (xh) B[o - dy - dx] = v;
+        }
+    }
 
     __device__ void strip_of(int s, int &c, int &row0, int &col0) const
     {
@@ -88,30 +158,107 @@ struct Eng {
         col0 = (rem - sy * cx.nx) * 32;
     }
 
-    // both orientations of kernel b (all channels) into shared memory, stored
-    // column-major per channel: w[c][q][p], p < Kp (rows beyond K are zero)
+    // TMA boxes of buffer b for the strip at (c, row0, col0); lane 0 only.
+    // Stage: tile rows trow .. trow+NX-1 (image rows row0 - r + trow ...), BW
+    // columns from image column col0 - r4; rows outside the padded image read 0.
+    __device__ void box_s(T *dst, int b, int c, int row0, int col0, int trow, uint64_t *mb) const
+    {
+        tma_load_4d(dst, &cx.map_s, col0 - cx.r4 + cx.Gx, row0 - cx.r + cx.Gy + trow, c, b, mb);
+    }
+    // halo-1 tile: rows row0-1 .. row0+MR, columns col0-4 .. col0+35 (pitch 40)
+    __device__ void box_1(T *dst, int b, int c, int row0, int col0, uint64_t *mb) const
+    {
+        tma_load_4d(dst, &cx.map_1, col0 - 4 + cx.Gx, row0 - 1 + cx.Gy, c, b, mb);
+    }
+    // interior: rows row0 .. row0+MR-1, columns col0 .. col0+31 (pitch 32)
+    __device__ void box_i(T *dst, int b, int c, int row0, int col0, uint64_t *mb) const
+    {
+        tma_load_4d(dst, &cx.map_i, col0 + cx.Gx, row0 + cx.Gy, c, b, mb);
+    }
+    __device__ unsigned bytes_s() const { return (unsigned)(cx.BW * NX * sizeof(T)); }
+    __device__ static constexpr unsigned bytes_1() { return (unsigned)(40 * (MR + 2) * sizeof(T)); }
+    __device__ static constexpr unsigned bytes_i() { return (unsigned)(32 * MR * sizeof(T)); }
+    __device__ T *sb(int i) const { return i ? sb1 : sb0; }
+
+    // wait for the copies on mbar[i]; warp-uniform result.  On a timeout the
+    // status is raised and the warp stops its TMA work (tmafail).
+    __device__ bool land(int i)
+    {
+        const unsigned ph = (mph >> i) & 1u;
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&mbar[i], ph, cx.timeout_ns));
+        if (!ok) {
+            if (lane == 0) raise(ST_TIMEOUT);
+            tmafail = true;
+            return false;
+        }
+        mph ^= 1u << i;
+        return true;
+    }
+
+    // bounded wait for whatever copies a failed warp may still have in flight
+    __device__ void drain()
+    {
+        if (!tmafail) return;
+        for (int i = 0; i < 2; ++i) mbar_wait(&mbar[i], (mph >> i) & 1u, cx.timeout_ns);
+    }
+
+    // lane 0: expect and issue stage k (buffer k & 1) of image img at tile row
+    // trow; extra(mb) issues more boxes (extra_bytes) on the same barrier
+    template <typename Extra>
+    __device__ void issue(int k, int img, int c, int row0, int col0, int trow, unsigned extra_bytes, Extra extra)
+    {
+        if (lane == 0) {
+            uint64_t *mb = &mbar[k & 1];
+            mbar_expect_tx(mb, bytes_s() + extra_bytes);
+            box_s(sb(k & 1), img, c, row0, col0, trow, mb);
+            extra(mb);
+        }
+    }
+
+    // both orientations of kernel b (all channels), column-major per channel:
+    // w[c][q][p], p < Kp (rows beyond K are zero).  When they fit (cx.wsm)
+    // each CTA keeps them in shared memory; otherwise all CTAs fill the global
+    // slot not used by the previous kernel and pass a grid barrier, and the
+    // correlation reads them through L1.  Either way the correlation loads
+    // them through the same (generic) pointers.
     __device__ void load_weights(const T *b)
     {
-        __syncthreads();
         const int K = cx.K, Kp = cx.Kp, KK = K * K, per = Kp * K, n = cx.C * per;
-        for (int e = tid; e < n; e += blockDim.x) {
-            const int c = e / per, rem = e - c * per, q = rem / Kp, p = rem - q * Kp;
+        T *F;
+        long long e0, st;
+        if (cx.wsm) {
+            __syncthreads();           // the previous kernel's readers are done
+            F = wsm;
+            e0 = tid;
+            st = blockDim.x;
+        } else {
+            wslot ^= 1;
+            F = cx.wg + (long long)wslot * 2 * n;
+            e0 = gstart();
+            st = gstride();
+        }
+        T *Tt = F + n;
+        for (long long e = e0; e < n; e += st) {
+            const int c = (int)(e / per), rem = (int)(e - (long long)c * per), q = rem / Kp, p = rem - q * Kp;
             T f = T(0), t = T(0);
             if (p < K) {
                 const T *bc = b + (long long)c * KK;
                 f = __ldcg(bc + (K - 1 - p) * K + (K - 1 - q));
                 t = __ldcg(bc + p * K + q);
             }
-            wF[e] = f;
-            wT[e] = t;
+            F[e] = f;
+            Tt[e] = t;
         }
-        __syncthreads();
+        wF = F;
+        wT = Tt;
+        if (cx.wsm) __syncthreads();
+        else sync();
     }
+
+    __device__ S *partS(int slot) const { return reinterpret_cast<S *>(cx.part) + slot * gridDim.x; }
 
     // record this CTA's partial in a slot and return the grid total after a
     // barrier; every CTA obtains identical bits
-    __device__ S *partS(int slot) const { return reinterpret_cast<S *>(cx.part) + slot * gridDim.x; }
-
     __device__ S reduce(S mine, int slot)
     {
         const S cta = block_sum<T>(mine, red);
@@ -120,148 +267,218 @@ struct Eng {
         return grid_total<T>(partS(slot), gridDim.x, gbuf, bcast);
     }
 
-    __device__ void stage_halo(T *dst, const T *src, long long cbase, int row0, int col0) const
+    // acc += correlation of stage buffer s (kernel rows p0 .. p0+PC-1)
+    __device__ void corr_on(const T *s, bool flip, int c, int p0, T (&acc)[MR]) const
     {
-        warp_stage(dst, cx.PA, cx.RA, cx.PA, src, cbase, row0 - cx.r, col0 - cx.r, cx.H, cx.W, lane);
+        const T *w = (flip ? wF : wT) + (long long)c * cx.Kp * cx.K + p0;
+        corr_stage<T, MR, PC>(s, cx.BW, w, cx.K, cx.Kp, lane + off, acc);
     }
 
-    __device__ void stage_halo1(T *dst, const T *src, long long cbase, int row0, int col0) const
-    {
-        warp_stage(dst, 34, MR + 2, 34, src, cbase, row0 - 1, col0 - 1, cx.H, cx.W, lane);
-    }
-
-    __device__ void corr(const T *tile, bool flip, int c, T (&acc)[MR]) const
-    {
-#pragma unroll
-        for (int m = 0; m < MR; ++m) acc[m] = T(0);
-        const T *w = (flip ? wF : wT) + c * cx.Kp * cx.K;
-        corr_strip<T, MR, Cfg<T>::PC>(tile, cx.PA, w, cx.K, cx.Kp, lane, acc);
-    }
-
-    // One convolution pass over all strips.  stage() issues the async copies of
-    // the strip (halo-r input into hA, extra tiles as needed); when fsrc is not
-    // null the strip's own pixels of fsrc (a per-pixel operand of the
-    // epilogue) are staged into tF with the same batch of copies; prep() runs
-    // on the staged tiles before the correlation; epi() consumes each in-image
-    // output (with its staged operand) and returns its share of a reduction
-    // (in the element type per strip, in the reduction scalar across strips).
-    template <typename Stage, typename Prep, typename Epi>
-    __device__ S pass(bool flip, Stage stage, const T *fsrc, Prep prep, Epi epi)
+    // One convolution pass over all strips.  img0 is staged in stages of NX
+    // rows (double-buffered).  With img1 >= 0 each stage holds img0 in sb0 and
+    // img1 in sb1 (single-buffered) and prep(stage, c, row0, col0) combines them
+    // into sb0 before the correlation.  The halo-1 tiles of t1b / t2b and the
+    // interior of fb (epilogue operands, any may be -1) are staged with the
+    // first stage.  epi(c, gi, gj, g, m, v, fv) consumes each in-image output v
+    // (dense index g, with fv the staged operand) and returns its share of a
+    // reduction (element type per strip, reduction scalar across strips).
+    template <typename Prep, typename Epi>
+    __device__ S pass(bool flip, int img0, int img1, int t1b, int t2b, int fb, Prep prep, Epi epi)
     {
         S part = Sc::zero();
+        if (!alive || tmafail) return part;
+        if (lane == 0) fence_proxy_async();
+        const bool two = img1 >= 0;
+        const unsigned eb = (t1b >= 0 ? bytes_1() : 0u) + (t2b >= 0 ? bytes_1() : 0u) + (fb >= 0 ? bytes_i() : 0u);
         for (int s = gw; s < cx.nstrips; s += TW) {
             int c, row0, col0;
             strip_of(s, c, row0, col0);
-            const long long cbase = (long long)c * cx.HW;
-            stage(c, row0, col0, cbase);
-            if (fsrc) warp_stage(tF, 32, MR, 32, fsrc, cbase, row0, col0, cx.H, cx.W, lane);
-            cp_async_wait_all();
-            __syncwarp();
-            prep(c, row0, col0, cbase);
-            __syncwarp();
+            auto extra = [&](uint64_t *mb) {
+                if (t1b >= 0) box_1(t1, t1b, c, row0, col0, mb);
+                if (t2b >= 0) box_1(t2, t2b, c, row0, col0, mb);
+                if (fb >= 0) box_i(tF, fb, c, row0, col0, mb);
+            };
             T acc[MR];
-            corr(hA, flip, c, acc);
+#pragma unroll
+            for (int m = 0; m < MR; ++m) acc[m] = T(0);
+            if (!two) {
+                issue(0, img0, c, row0, col0, 0, eb, extra);
+                for (int st = 0; st < ns; ++st) {
+                    if (!land(st & 1)) return part;
+                    if (st + 1 < ns) issue(st + 1, img0, c, row0, col0, (st + 1) * PC, 0u, [](uint64_t *) {});
+                    corr_on(sb(st & 1), flip, c, st * PC, acc);
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                }
+            } else {
+                for (int st = 0; st < ns; ++st) {
+                    if (lane == 0) {
+                        uint64_t *mb = &mbar[0];
+                        mbar_expect_tx(mb, 2 * bytes_s() + (st == 0 ? eb : 0u));
+                        box_s(sb0, img0, c, row0, col0, st * PC, mb);
+                        box_s(sb1, img1, c, row0, col0, st * PC, mb);
+                        if (st == 0) extra(mb);
+                    }
+                    if (!land(0)) return part;
+                    prep(st, c, row0, col0);
+                    __syncwarp();
+                    corr_on(sb0, flip, c, st * PC, acc);
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                }
+            }
             T sum = T(0);
             const int gj = col0 + lane;
+            const long long cbase = (long long)c * cx.HW;
 #pragma unroll
             for (int m = 0; m < MR; ++m) {
                 const int gi = row0 + m;
                 if (gi < cx.H && gj < cx.W)
-                    sum += epi(c, m, cbase + (long long)gi * cx.W + gj, acc[m], tF[m * 32 + lane]);
+                    sum += epi(c, gi, gj, cbase + (long long)gi * cx.W + gj, m, acc[m], tF[m * 32 + lane]);
             }
             part = Sc::addv(part, sum);
+            fence_proxy_async_smem();      // epilogue reads before the next strip's copies
             __syncwarp();
         }
         return part;
     }
 
-    // TV gradient at strip pixel (m, lane) of a halo-1 tile s (pitch 34)
+    // TV gradient at strip pixel (m, lane) of a halo-1 tile s (pitch 40,
+    // column 0 = image column col0 - 4)
     __device__ T tv_grad(const T *s, int m) const
     {
         const T g = cx.rpT, ig = cx.irpT;
-        const int o = (m + 1) * 34 + lane + 1;
+        const int o = (m + 1) * 40 + lane + 4;
         const T yc = s[o];
         return dphi<T>(cx.reg, yc - s[o - 1], g, ig) - dphi<T>(cx.reg, s[o + 1] - yc, g, ig) +
-               dphi<T>(cx.reg, yc - s[o - 34], g, ig) - dphi<T>(cx.reg, s[o + 34] - yc, g, ig);
+               dphi<T>(cx.reg, yc - s[o - 40], g, ig) - dphi<T>(cx.reg, s[o + 40] - yc, g, ig);
     }
 
     // D^T(phi''(D x) . D v) at strip pixel (m, lane); x in sx, v in sv (halo 1)
     __device__ T tv_hess(const T *sx, const T *sv, int m) const
     {
         const T g = cx.rpT, ig = cx.irpT;
-        const int o = (m + 1) * 34 + lane + 1;
+        const int o = (m + 1) * 40 + lane + 4;
         const T xc = sx[o], vc = sv[o];
         const T wl = ddphi<T>(cx.reg, xc - sx[o - 1], g, ig);
         const T wr = ddphi<T>(cx.reg, sx[o + 1] - xc, g, ig);
-        const T wu = ddphi<T>(cx.reg, xc - sx[o - 34], g, ig);
-        const T wd = ddphi<T>(cx.reg, sx[o + 34] - xc, g, ig);
-        return wl * (vc - sv[o - 1]) - wr * (sv[o + 1] - vc) + wu * (vc - sv[o - 34]) - wd * (sv[o + 34] - vc);
+        const T wu = ddphi<T>(cx.reg, xc - sx[o - 40], g, ig);
+        const T wd = ddphi<T>(cx.reg, sx[o + 40] - xc, g, ig);
+        return wl * (vc - sv[o - 1]) - wr * (sv[o + 1] - vc) + wu * (vc - sv[o - 40]) - wd * (sv[o + 40] - vc);
+    }
+
+    __device__ T center1(const T *s, int m) const { return s[(m + 1) * 40 + lane + 4]; }
+
+    // ------------------------------------------------------------ import / export
+    // dense caller image -> buffer b (with ghosts); a warp per image row
+    __device__ void import_dense(const T *src, int b)
+    {
+        T *B = buf(b);
+        for (int row = gw; row < cx.C * cx.H; row += TW) {
+            const int c = row / cx.H, i = row - c * cx.H;
+            const T *sr = src + (long long)row * cx.W;
+            for (int j = lane; j < cx.W; j += 32) put(B, c, i, j, __ldcg(sr + j));
+        }
+    }
+
+    // buffer b -> dense caller image; a warp per image row
+    __device__ void export_dense(int b, T *dst)
+    {
+        const T *B = buf(b);
+        for (int row = gw; row < cx.C * cx.H; row += TW) {
+            const int c = row / cx.H, i = row - c * cx.H;
+            T *dr = dst + (long long)row * cx.W;
+            const T *br = B + pidx(c, i, 0);
+            for (int j = lane; j < cx.W; j += 32) dr[j] = __ldcg(br + j);
+        }
+    }
+
+    // dst = src (and dst2 = src) over whole padded buffers, ghosts included
+    __device__ void copy_buf(int dst, int dst2, int src)
+    {
+        const T *Sp = buf(src);
+        T *D = buf(dst), *D2 = dst2 >= 0 ? buf(dst2) : nullptr;
+        const long long N = cx.Np, st = gstride();
+        for (long long base = gstart(); base < N; base += EWB * st) {
+            T v[EWB];
+#pragma unroll
+            for (int u = 0; u < EWB; ++u) {
+                const long long i = base + u * st;
+                v[u] = i < N ? __ldcg(Sp + i) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < EWB; ++u) {
+                const long long i = base + u * st;
+                if (i < N) {
+                    D[i] = v[u];
+                    if (D2) D2[i] = v[u];
+                }
+            }
+        }
     }
 
     // ------------------------------------------------------------ programs
-    __device__ void apply(const T *b, const T *x, T *out, bool transpose)
+    struct NoPrep {
+        __device__ void operator()(int, int, int, int) const {}
+    };
+    static constexpr NoPrep noprep{};
+
+    // out = B x (flip) or B^T x; x in buffer bx, weights of b loaded
+    __device__ void apply(int bx, T *out, bool transpose)
     {
-        load_weights(b);
-        pass(!transpose, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, x, cbase, row0, col0); },
-             nullptr, [](int, int, int, long long) {},
-             [=](int, int, long long g, T v, T) { out[g] = v; return T(0); });
+        pass(!transpose, bx, -1, -1, -1, -1, noprep,
+             [=](int, int, int, long long g, int, T v, T) { out[g] = v; return T(0); });
     }
 
-    // U = B x - y (weights of b loaded)
-    __device__ void residual(const T *x, T *U)
+    // buffer bu = B x - y (weights of b loaded)
+    __device__ void residual(int bx, int bu)
     {
-        const T *y = cx.y;
-        pass(true, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, x, cbase, row0, col0); },
-             y, [](int, int, int, long long) {},
-             [=](int, int, long long g, T v, T yv) { U[g] = v - yv; return T(0); });
+        T *U = buf(bu);
+        pass(true, bx, -1, -1, -1, B_Y, noprep,
+             [=](int c, int gi, int gj, long long, int, T v, T yv) { put(U, c, gi, gj, v - yv); return T(0); });
     }
 
-    __device__ void grad_lower(const T *b, const T *x, T *out)
+    // grad_x h = B^T(B x - y) + alpha grad J(x) into dense out (may be null);
+    // its norm into the result record
+    __device__ void grad_lower(const T *b, int bx, T *out)
     {
         load_weights(b);
-        residual(x, cx.U);
+        residual(bx, B_U);
         if (!sync()) return;
         const T al = cx.alphaT;
-        const T *U = cx.U;
-        const S part = pass(
-            false,
-            [=](int, int row0, int col0, long long cbase) {
-                stage_halo(hA, U, cbase, row0, col0);
-                stage_halo1(t1, x, cbase, row0, col0);
-            },
-            nullptr, [](int, int, int, long long) {},
-            [=](int, int m, long long g, T v, T) {
-                const T gr = v + al * tv_grad(t1, m);
-                if (out) out[g] = gr;
-                return gr * gr;
-            });
+        const S part = pass(false, B_U, -1, bx, -1, -1, noprep, [=](int, int, int, long long g, int m, T v, T) {
+            const T gr = v + al * tv_grad(t1, m);
+            if (out) out[g] = gr;
+            return gr * gr;
+        });
         const S ss = reduce(part, 0);
         if (alive && tid == 0 && blockIdx.x == 0) cx.out->gradnorm = sqrt(Sc::to_double(ss));
     }
 
-    // out = B^T B v + alpha D^T(phi''(D x) . D v) (weights of b loaded); returns
-    // this CTA's share of <v, out>
-    __device__ S hess_vec(const T *x, const T *v, T *out)
+    // B^T B v + alpha D^T(phi''(D x) . D v) for x, v in buffers bx, bv: to
+    // buffer bo (with ghosts) or, when dense_out is set, to the caller's image.
+    // Returns this warp's share of <v, out>.  Weights of b loaded.
+    __device__ S hess_vec(int bx, int bv, int bo, T *dense_out)
+    {
+        T *U = buf(B_U);
+        pass(true, bv, -1, -1, -1, -1, noprep,
+             [=](int c, int gi, int gj, long long, int, T val, T) { put(U, c, gi, gj, val); return T(0); });
+        if (!sync()) return Sc::zero();
+        return hess_vec_b(bx, bv, bo, dense_out);
+    }
+
+    // second half of a Hessian-vector product whose first half (U = B v) is
+    // done: out = B^T U + alpha D^T(phi''(D x) . D v); <v, out>
+    __device__ S hess_vec_b(int bx, int bv, int bo, T *dense_out)
     {
         const T al = cx.alphaT;
-        T *U = cx.U;
-        pass(true, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, v, cbase, row0, col0); },
-             nullptr, [](int, int, int, long long) {},
-             [=](int, int, long long g, T val, T) { U[g] = val; return T(0); });
-        if (!sync()) return Sc::zero();
-        return pass(
-            false,
-            [=](int, int row0, int col0, long long cbase) {
-                stage_halo(hA, U, cbase, row0, col0);
-                stage_halo1(t1, x, cbase, row0, col0);
-                stage_halo1(t2, v, cbase, row0, col0);
-            },
-            nullptr, [](int, int, int, long long) {},
-            [=](int, int m, long long g, T val, T) {
-                const T hv = val + al * tv_hess(t1, t2, m);
-                out[g] = hv;
-                return hv * t2[(m + 1) * 34 + lane + 1];
-            });
+        T *O = buf(bo);
+        return pass(false, B_U, -1, bx, bv, -1, noprep, [=](int c, int gi, int gj, long long g, int m, T v, T) {
+            const T hv = v + al * tv_hess(t1, t2, m);
+            if (dense_out) dense_out[g] = hv;
+            else put(O, c, gi, gj, hv);
+            return hv * center1(t2, m);
+        });
     }
 
     // 1/L_c for FISTA on channel c with kernel b: L_c = ||b_c||_1^2 + 8 alpha sup phi''
@@ -281,48 +498,31 @@ struct Eng {
         __syncthreads();
     }
 
-    // dst[i] = src[i] (and dst2[i] = src[i] if dst2), loads issued EWB at a time
-    __device__ void copy_img(T *dst, T *dst2, const T *src)
-    {
-        const long long N = cx.N, st = gstride();
-        for (long long base = gstart(); base < N; base += EWB * st) {
-            T v[EWB];
-#pragma unroll
-            for (int u = 0; u < EWB; ++u) { const long long i = base + u * st; v[u] = i < N ? __ldcg(src + i) : T(0); }
-#pragma unroll
-            for (int u = 0; u < EWB; ++u) {
-                const long long i = base + u * st;
-                if (i < N) { dst[i] = v[u]; if (dst2) dst2[i] = v[u]; }
-            }
-        }
-    }
-
     // t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, the FISTA momentum sequence
     __device__ S next_t(S t) const
     {
         return Sc::mul(Sc::addv(Sc::sqroot(Sc::addv(Sc::mul(Sc::of(4), Sc::mul(t, t)), 1)), 1), Sc::of(0.5));
     }
 
-    // FISTA (Algorithm 1, step 1) from x_in to x_out: returns updates made.
-    // The momentum theta_{k+1} = (t_k - 1)/t_{k+1} does not depend on the data,
-    // so pass B writes both x_{k+1} and y_{k+1}.  The stopping test on
-    // ||grad_x h(y_k)|| is read one pass late: the partial sums of iteration k
-    // are fetched while pass A of iteration k+1 runs, and when the test holds
-    // y_k (still in its own buffer) is returned and that pass A is discarded.
-    __device__ int lower_solve(const T *b, const T *x_in, T *x_out, double eps, int max_iters, double &gn,
+    // FISTA (Algorithm 1, step 1) from buffer bin (warm start) to buffer bout:
+    // returns updates made.  The momentum theta_{k+1} = (t_k - 1)/t_{k+1} does
+    // not depend on the data, so pass B writes both x_{k+1} and y_{k+1}.  The
+    // stopping test on ||grad_x h(y_k)|| is read one pass late: the partial sums
+    // of iteration k are fetched while pass A of iteration k+1 runs, and when
+    // the test holds y_k (still in its own buffer) is returned and that pass A
+    // is discarded.  bin may equal bout.
+    __device__ int lower_solve(const T *b, int bin, int bout, double eps, int max_iters, double &gn,
                                long long &passes)
     {
         load_weights(b);
         compute_tau(b);
-        copy_img(cx.X0, cx.Y0, x_in);
+        copy_buf(B_X0, B_Y0, bin);
         if (!sync()) return 0;
-        T *xp = cx.X0, *xn = cx.X1, *yc = cx.Y0, *yn = cx.Y1, *U = cx.U;
-        const T *y = cx.y;
+        int xp = B_X0, xn = B_X1, yc = B_Y0, yn = B_Y1;
         const T al = cx.alphaT;
         const T *tauc = tau;
-        const T *result = nullptr;
+        int result = -1;
         const S eps2 = Sc::from_double(eps * eps);
-        // momentum sequence t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2 in the control scalar
         // theta_{k+1} for the first iteration (t_0 = 1); later ones are computed
         // while a barrier is pending
         S t = Sc::of(1);
@@ -331,12 +531,10 @@ struct Eng {
         bool pending = false;
         int k = 0;
         for (;; ++k) {
-            const T *ycur = yc;
+            const int ycur = yc;
             if (pending && warp == 0) grid_issue<T>(partS((k - 1) & 1), gridDim.x, gbuf);
             // phase A: U = B y_k - y
-            pass(true, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, ycur, cbase, row0, col0); },
-                 y, [](int, int, int, long long) {},
-                 [=](int, int, long long g, T v, T yv) { U[g] = v - yv; return T(0); });
+            residual(ycur, B_U);
             if (pending) {
                 if (warp == 0) {
                     const S s = grid_finish<T>(gridDim.x, gbuf);
@@ -345,7 +543,11 @@ struct Eng {
                 __syncthreads();
                 const S sprev = *bcast;
                 __syncthreads();
-                if (!Sc::finite(sprev)) { fail(ST_NONFINITE); return k - 1; }
+                if (!Sc::finite(sprev)) {
+                    if (tid == 0) raise(ST_NONFINITE);
+                    alive = false;
+                    return k - 1;
+                }
                 if (Sc::le(sprev, eps2)) {     // y_{k-1} passes: keep it, drop this pass A
                     gn = sqrt(Sc::to_double(sprev));
                     result = yn;
@@ -356,22 +558,16 @@ struct Eng {
             if (!sync()) return k;
             // phase B: G = B^T U + alpha grad J(y_k); x_{k+1} = y_k - tau_c G;
             // y_{k+1} = x_{k+1} + theta_{k+1} (x_{k+1} - x_k); ||G||^2
-            T *xnl = xn, *ynl = yn;
-            const T *xpl = xp;
-            const S part = pass(
-                false,
-                [=](int, int row0, int col0, long long cbase) {
-                    stage_halo(hA, U, cbase, row0, col0);
-                    stage_halo1(t1, ycur, cbase, row0, col0);
-                },
-                xpl, [](int, int, int, long long) {},
-                [=](int c, int m, long long g, T v, T xpv) {
-                    const T gr = v + al * tv_grad(t1, m);
-                    const T xnv = t1[(m + 1) * 34 + lane + 1] - tauc[c] * gr;
-                    xnl[g] = xnv;
-                    ynl[g] = xnv + thn * (xnv - xpv);
-                    return gr * gr;
-                });
+            T *XN = buf(xn), *YN = buf(yn);
+            const T th = thn;
+            const S part = pass(false, B_U, -1, ycur, -1, xp, noprep,
+                                [=](int c, int gi, int gj, long long, int m, T v, T xpv) {
+                                    const T gr = v + al * tv_grad(t1, m);
+                                    const T xnv = center1(t1, m) - tauc[c] * gr;
+                                    put(XN, c, gi, gj, xnv);
+                                    put(YN, c, gi, gj, xnv + th * (xnv - xpv));
+                                    return gr * gr;
+                                });
             const S cta = block_sum<T>(part, red);
             if (tid == 0) partS(k & 1)[blockIdx.x] = cta;
             // momentum of the next iteration, before waiting on the barrier
@@ -382,7 +578,11 @@ struct Eng {
             passes += 2;
             if (k >= max_iters) {          // cap: the norm of y_k is needed now
                 const S ss = grid_total<T>(partS(k & 1), gridDim.x, gbuf, bcast);
-                if (!Sc::finite(ss)) { fail(ST_NONFINITE); return k; }
+                if (!Sc::finite(ss)) {
+                    if (tid == 0) raise(ST_NONFINITE);
+                    alive = false;
+                    return k;
+                }
                 gn = sqrt(Sc::to_double(ss));
                 result = yc;
                 break;
@@ -391,10 +591,10 @@ struct Eng {
             t = t_next;
             tn = tn_next;
             thn = thn_next;
-            T *tmp = xp; xp = xn; xn = tmp;
+            int tmp = xp; xp = xn; xn = tmp;
             tmp = yc; yc = yn; yn = tmp;
         }
-        copy_img(x_out, nullptr, result);
+        if (result != bout) copy_buf(bout, -1, result);
         return k;
     }
 
@@ -431,75 +631,84 @@ struct Eng {
         return 2.0 * cx.beta * (cx.w0 * d + dh_prev - dh_here + dv_prev - dv_here);
     }
 
-    // ell = g(x) + r(b) and ||grad g(x)||; grad g stored in cx.G
-    __device__ void upper_loss(const T *b, const T *x, double &loss, double &gxn, long long &passes)
+    // ell = g(x) + r(b) and ||grad g(x)|| for x in buffer bx; grad g = 2 A^T(A x - y)
+    // stored in buffer B_G (with ghosts)
+    __device__ void upper_loss(const T *b, int bx, double &loss, double &gxn, long long &passes)
     {
         // r(b) first: b may be rewritten by other CTAs right after the last
         // barrier of this function (the next backtracking trial)
         const double rb = sobolev(b);
         load_weights(cx.a);
-        const T *y = cx.y;
-        T *V = cx.V, *G = cx.G;
-        const S pg = pass(
-            true, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, x, cbase, row0, col0); },
-            y, [](int, int, int, long long) {},
-            [=](int, int, long long g, T v, T yv) {
-                const T e = v - yv;
-                V[g] = e;
-                return e * e;
-            });
+        T *V = buf(B_V), *G = buf(B_G);
+        const S pg = pass(true, bx, -1, -1, -1, B_Y, noprep, [=](int c, int gi, int gj, long long, int, T v, T yv) {
+            const T e = v - yv;
+            put(V, c, gi, gj, e);
+            return e * e;
+        });
         const S gval = reduce(pg, 2);
         if (!alive) return;
-        const S pgg = pass(
-            false, [=](int, int row0, int col0, long long cbase) { stage_halo(hA, V, cbase, row0, col0); },
-            nullptr, [](int, int, int, long long) {},
-            [=](int, int, long long g, T v, T) {
-                const T gg = T(2) * v;
-                G[g] = gg;
-                return gg * gg;
-            });
+        const S pgg = pass(false, B_V, -1, -1, -1, -1, noprep, [=](int c, int gi, int gj, long long, int, T v, T) {
+            const T gg = T(2) * v;
+            put(G, c, gi, gj, gg);
+            return gg * gg;
+        });
         const S ggs = reduce(pgg, 3);
         if (!alive) return;
         passes += 2;
         loss = Sc::to_double(gval) + rb;
         gxn = sqrt(Sc::to_double(ggs));
-        if (!isfinite(loss) || !isfinite(gxn)) fail(ST_NONFINITE);
+        if (!isfinite(loss) || !isfinite(gxn)) {
+            if (tid == 0) raise(ST_NONFINITE);
+            alive = false;
+        }
     }
 
-    // CG (Algorithm 1, step 2) on H(x, b) q = rhs from the q held in Q
-    // (zero_start: Q is taken as zero).  The direction update p = r + beta p of
-    // iteration k is fused into the B p pass of iteration k+1 (computed on the
-    // staged halo tiles of r and the previous p).  Returns iterations.
-    __device__ int cg(const T *b, const T *x, const T *rhs, T *Q, double delta, int max_iters, bool zero_start,
-                      double &res, int &capped, long long &passes)
+    // CG (Algorithm 1, step 2) on grad^2_x h(x, b) q = rhs with x in buffer bx,
+    // rhs in brhs and q in B_Q (taken as zero when zero_start).  The direction
+    // update p = r + beta p of iteration k is fused into the B p pass of
+    // iteration k+1: each stage holds r and the previous p, combined in shared
+    // memory, and the strip's own rows of p are written back.  Element-wise
+    // updates run over whole padded buffers (ghosts stay current); sums count
+    // image pixels only.  Returns iterations.
+    __device__ int cg(const T *b, int bx, int brhs, double delta, int max_iters, bool zero_start, double &res,
+                      int &capped, long long &passes)
     {
         load_weights(b);
-        T *R = cx.R, *HP = cx.HP, *U = cx.U;
-        T *pc = cx.P0, *po = cx.P1;
-        S rrp = Sc::zero();
-        const long long N = cx.N, st = gstride();
+        T *R = buf(B_R), *HP = buf(B_HP), *Q = buf(B_Q);
+        const T *RHS = buf(brhs);
+        int pc = B_P0, po = B_P1;
         if (!zero_start) {
-            hess_vec(x, Q, HP);
+            hess_vec(bx, B_Q, B_HP, nullptr);
             if (!sync()) return 0;
             passes += 2;
         }
+        auto interior = [&](int row, int j) {
+            const int pi = row % cx.Hp;
+            return pi >= cx.Gy && pi < cx.Gy + cx.H && j >= cx.Gx && j < cx.Gx + cx.W;
+        };
+        S rrp = Sc::zero();
         {
-            for (long long base = gstart(); base < N; base += EWB * st) {
-                T v[EWB];
+            T *PCb = buf(pc);
+            for (int row = gw; row < cx.C * cx.Hp; row += TW) {
+                const long long rb = (long long)row * cx.Wp;
                 T s = T(0);
+                for (int j0 = 0; j0 < cx.Wp; j0 += 32 * EWB) {
+                    T v[EWB];
 #pragma unroll
-                for (int u = 0; u < EWB; ++u) {
-                    const long long i = base + u * st;
-                    v[u] = i < N ? (zero_start ? __ldcg(rhs + i) : __ldcg(rhs + i) - __ldcg(HP + i)) : T(0);
-                }
+                    for (int u = 0; u < EWB; ++u) {
+                        const int j = j0 + u * 32 + lane;
+                        v[u] = j < cx.Wp ? (zero_start ? __ldcg(RHS + rb + j) : __ldcg(RHS + rb + j) - __ldcg(HP + rb + j))
+                                         : T(0);
+                    }
 #pragma unroll
-                for (int u = 0; u < EWB; ++u) {
-                    const long long i = base + u * st;
-                    if (i < N) {
-                        if (zero_start) Q[i] = T(0);
-                        R[i] = v[u];
-                        pc[i] = v[u];
-                        s += v[u] * v[u];
+                    for (int u = 0; u < EWB; ++u) {
+                        const int j = j0 + u * 32 + lane;
+                        if (j < cx.Wp) {
+                            if (zero_start) Q[rb + j] = T(0);
+                            R[rb + j] = v[u];
+                            PCb[rb + j] = v[u];
+                            if (interior(row, j)) s += v[u] * v[u];
+                        }
                     }
                 }
                 rrp = Sc::addv(rrp, s);
@@ -512,89 +721,85 @@ struct Eng {
         capped = 0;
         bool first = true;
         T beta = T(0);
-        const T al = cx.alphaT;
+        T *U = buf(B_U);
         while (!Sc::le(rr, delta2) && it < max_iters) {
             // phase A: p (fused update unless first) and U = B p
-            T *pcl = pc;
-            const T *pol = po;
-            const bool fst = first;
+            T *PW = buf(pc);
             const T bt = beta;
-            pass(
-                true,
-                [=](int, int row0, int col0, long long cbase) {
-                    if (fst) {
-                        stage_halo(hA, pcl, cbase, row0, col0);
-                    } else {
-                        stage_halo(hA, R, cbase, row0, col0);
-                        stage_halo(hB, pol, cbase, row0, col0);
-                    }
-                },
-                nullptr,
-                [=](int, int row0, int col0, long long cbase) {
-                    if (fst) return;
-                    const int n = cx.RA * cx.PA;
-                    for (int e = lane; e < n; e += 32) hA[e] = hA[e] + bt * hB[e];
-                    __syncwarp();
-                    const int gj = col0 + lane;
-                    for (int m = 0; m < MR; ++m) {
-                        const int gi = row0 + m;
-                        if (gi < cx.H && gj < cx.W)
-                            pcl[cbase + (long long)gi * cx.W + gj] = hA[(m + cx.r) * cx.PA + lane + cx.r];
-                    }
-                },
-                [=](int, int, long long g, T v, T) { U[g] = v; return T(0); });
+            const int BWl = cx.BW, r = cx.r, r4 = cx.r4;
+            auto combine = [=](int st, int c, int row0, int col0) {
+                const int n = NX * BWl;
+                for (int e = lane; e < n; e += 32) sb0[e] = sb0[e] + bt * sb1[e];
+                __syncwarp();
+                // the strip's own rows (tile rows r .. r+MR-1) that this stage owns
+                const int gj = col0 + lane;
+                for (int m = 0; m < MR; ++m) {
+                    const int t = r + m;
+                    if (t < st * PC || t >= (st + 1) * PC) continue;
+                    const int gi = row0 + m;
+                    if (gi < cx.H && gj < cx.W) put(PW, c, gi, gj, sb0[(t - st * PC) * BWl + r4 + lane]);
+                }
+            };
+            auto epiU = [=](int c, int gi, int gj, long long, int, T v, T) { put(U, c, gi, gj, v); return T(0); };
+            if (first) pass(true, pc, -1, -1, -1, -1, noprep, epiU);
+            else pass(true, B_R, po, -1, -1, -1, combine, epiU);
             if (!sync()) return it;
             // phase B: HP = B^T U + alpha D^T(phi''(D x) . D p); <p, HP>
-            const S php = reduce(
-                pass(
-                    false,
-                    [=](int, int row0, int col0, long long cbase) {
-                        stage_halo(hA, U, cbase, row0, col0);
-                        stage_halo1(t1, x, cbase, row0, col0);
-                        stage_halo1(t2, pcl, cbase, row0, col0);
-                    },
-                    nullptr, [](int, int, int, long long) {},
-                    [=](int, int m, long long g, T v, T) {
-                        const T hv = v + al * tv_hess(t1, t2, m);
-                        HP[g] = hv;
-                        return hv * t2[(m + 1) * 34 + lane + 1];
-                    }),
-                5);
+            const S php = reduce(hess_vec_b(bx, pc, B_HP, nullptr), 5);
             if (!alive) return it;
             passes += 2;
-            if (!Sc::finite(php)) { fail(ST_NONFINITE); return it; }
+            if (!Sc::finite(php)) {
+                if (tid == 0) raise(ST_NONFINITE);
+                alive = false;
+                return it;
+            }
             if (!Sc::positive(php)) { capped = 1; break; }
             const T a = (T)Sc::to_elem(Sc::div(rr, php));
             S rn = Sc::zero();
-            for (long long base = gstart(); base < N; base += EWB * st) {
-                T pv[EWB], qv[EWB], rv[EWB], hv[EWB];
-                T s = T(0);
+            {
+                const T *PCr = buf(pc);
+                for (int row = gw; row < cx.C * cx.Hp; row += TW) {
+                    const long long rb = (long long)row * cx.Wp;
+                    T s = T(0);
+                    for (int j0 = 0; j0 < cx.Wp; j0 += 32 * EWB) {
+                        T pv[EWB], qv[EWB], rv[EWB], hv[EWB];
 #pragma unroll
-                for (int u = 0; u < EWB; ++u) {
-                    const long long i = base + u * st;
-                    if (i < N) { pv[u] = __ldcg(pcl + i); qv[u] = __ldcg(Q + i); rv[u] = __ldcg(R + i); hv[u] = __ldcg(HP + i); }
-                }
+                        for (int u = 0; u < EWB; ++u) {
+                            const int j = j0 + u * 32 + lane;
+                            if (j < cx.Wp) {
+                                pv[u] = __ldcg(PCr + rb + j);
+                                qv[u] = __ldcg(Q + rb + j);
+                                rv[u] = __ldcg(R + rb + j);
+                                hv[u] = __ldcg(HP + rb + j);
+                            }
+                        }
 #pragma unroll
-                for (int u = 0; u < EWB; ++u) {
-                    const long long i = base + u * st;
-                    if (i < N) {
-                        Q[i] = qv[u] + a * pv[u];
-                        const T r2 = rv[u] - a * hv[u];
-                        R[i] = r2;
-                        s += r2 * r2;
+                        for (int u = 0; u < EWB; ++u) {
+                            const int j = j0 + u * 32 + lane;
+                            if (j < cx.Wp) {
+                                Q[rb + j] = qv[u] + a * pv[u];
+                                const T r2 = rv[u] - a * hv[u];
+                                R[rb + j] = r2;
+                                if (interior(row, j)) s += r2 * r2;
+                            }
+                        }
                     }
+                    rn = Sc::addv(rn, s);
                 }
-                rn = Sc::addv(rn, s);
             }
             const S rr_new = reduce(rn, 6);
             if (!alive) return it;
             ++it;
-            if (!Sc::finite(rr_new)) { fail(ST_NONFINITE); return it; }
+            if (!Sc::finite(rr_new)) {
+                if (tid == 0) raise(ST_NONFINITE);
+                alive = false;
+                return it;
+            }
             if (Sc::le(rr_new, delta2)) { rr = rr_new; break; }
             beta = (T)Sc::to_elem(Sc::div(rr_new, rr));
             rr = rr_new;
             po = pc;
-            pc = (pc == cx.P0) ? cx.P1 : cx.P0;
+            pc = (pc == B_P0) ? B_P1 : B_P0;
             first = false;
         }
         res = sqrt(Sc::to_double(rr));
@@ -604,107 +809,140 @@ struct Eng {
 
     // out[c,p,q] = sum_ij x[c,i-p+r,j-q+r] (B v)[c,i,j] + v[c,i-p+r,j-q+r] (B x - y)[c,i,j]
     // (Algorithm 1, step 3, with the sign of Eq. 3.2: z = -out (+ grad r(b)));
-    // written to zout; returns ||zout||^2
-    __device__ double cross(const T *b, const T *x, const T *v, T *zout, bool negate, bool add_r, long long &passes)
+    // x, v in buffers bx, bv; written to zout; returns ||zout||^2
+    __device__ double cross(const T *b, int bx, int bv, T *zout, bool negate, bool add_r, long long &passes)
     {
         load_weights(b);
-        const T *y = cx.y;
-        T *U = cx.U, *V = cx.V;
+        T *U = buf(B_U), *V = buf(B_V);
         const int r = cx.r, K = cx.K, KK = K * K, H = cx.H, W = cx.W;
         const int CKK = cx.C * KK;
         S *zall = reinterpret_cast<S *>(cx.zpart);
         S *zp = zall + (long long)gw * CKK;
         for (int e = lane; e < CKK; e += 32) zp[e] = Sc::zero();
-        // phase K1: U = B v, V = B x - y
-        for (int s = gw; s < cx.nstrips; s += TW) {
-            int c, row0, col0;
-            strip_of(s, c, row0, col0);
-            const long long cbase = (long long)c * cx.HW;
-            stage_halo(hA, v, cbase, row0, col0);
-            stage_halo(hB, x, cbase, row0, col0);
-            const int gj = col0 + lane;
-            T yv[MR];
+        // phase K1: U = B v, V = B x - y (image pixels only: phase K2 reads
+        // interiors).  The stages of v and then of x run through the same
+        // double buffer.
+        if (!tmafail && alive) {
+            if (lane == 0) fence_proxy_async();
+            for (int s = gw; s < cx.nstrips; s += TW) {
+                int c, row0, col0;
+                strip_of(s, c, row0, col0);
+                T au[MR], av[MR];
 #pragma unroll
-            for (int m = 0; m < MR; ++m) {
-                const int gi = row0 + m;
-                yv[m] = (gi < H && gj < W) ? __ldg(y + cbase + (long long)gi * W + gj) : T(0);
-            }
-            cp_async_wait_all();
-            __syncwarp();
-            T au[MR], av[MR];
-            corr(hA, true, c, au);
-            corr(hB, true, c, av);
-#pragma unroll
-            for (int m = 0; m < MR; ++m) {
-                const int gi = row0 + m;
-                if (gi < H && gj < W) {
-                    const long long g = cbase + (long long)gi * W + gj;
-                    U[g] = au[m];
-                    V[g] = av[m] - yv[m];
+                for (int m = 0; m < MR; ++m) { au[m] = T(0); av[m] = T(0); }
+                issue(0, bv, c, row0, col0, 0, bytes_i(), [&](uint64_t *mb) { box_i(tF, B_Y, c, row0, col0, mb); });
+                bool ok = true;
+                for (int k = 0; k < 2 * ns; ++k) {
+                    if (!land(k & 1)) { ok = false; break; }
+                    if (k + 1 < 2 * ns) {
+                        const int kn = k + 1;
+                        issue(kn, kn < ns ? bv : bx, c, row0, col0, (kn < ns ? kn : kn - ns) * PC, 0u,
+                              [](uint64_t *) {});
+                    }
+                    if (k < ns) corr_on(sb(k & 1), true, c, k * PC, au);
+                    else corr_on(sb(k & 1), true, c, (k - ns) * PC, av);
+                    fence_proxy_async_smem();
+                    __syncwarp();
                 }
+                if (!ok) break;
+                const int gj = col0 + lane;
+#pragma unroll
+                for (int m = 0; m < MR; ++m) {
+                    const int gi = row0 + m;
+                    if (gi < H && gj < W) {
+                        const long long o = pidx(c, gi, gj);
+                        U[o] = au[m];
+                        V[o] = av[m] - tF[m * 32 + lane];
+                    }
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
             }
-            __syncwarp();
         }
         if (!sync()) return 0.0;
-        // phase K2: lag sums of this warp's strips.  A lane owns lag row p and
-        // QB consecutive lag columns q0..q0+QB-1; along each strip row the x and
-        // v windows slide through registers (one new shared load each per column).
-        const int nqb = (K + QB - 1) / QB, units = K * nqb;
-        for (int s = gw; s < cx.nstrips; s += TW) {
-            int c, row0, col0;
-            strip_of(s, c, row0, col0);
-            const long long cbase = (long long)c * cx.HW;
-            stage_halo(hA, x, cbase, row0, col0);
-            stage_halo(hB, v, cbase, row0, col0);
-            const int gj = col0 + lane;
-            for (int m = 0; m < MR; ++m) {
-                const int gi = row0 + m;
-                const bool in = gi < H && gj < W;
-                const long long g = cbase + (long long)gi * W + gj;
-                t1[m * 32 + lane] = in ? __ldcg(U + g) : T(0);
-                t2[m * 32 + lane] = in ? __ldcg(V + g) : T(0);
-            }
-            cp_async_wait_all();
-            __syncwarp();
-            for (int u = lane; u < units; u += 32) {
-                const int p = u / nqb, q0 = (u - p * nqb) * QB;
-                S acc[QB];
-#pragma unroll
-                for (int k = 0; k < QB; ++k) acc[k] = Sc::zero();
-                for (int m = 0; m < MR; ++m) {
-                    const T *rx = hA + (m + 2 * r - p) * cx.PA;
-                    const T *rv = hB + (m + 2 * r - p) * cx.PA;
-                    const T *ur = t1 + m * 32, *vr = t2 + m * 32;
-                    const int c0 = 2 * r - q0;       // column of lag q0 at j = 0
-                    T wx[QB], wv[QB], af[QB];
-#pragma unroll
-                    for (int k = 0; k < QB; ++k) af[k] = T(0);
-#pragma unroll
-                    for (int k = 1; k < QB; ++k) {
-                        const int col = c0 - k >= 0 ? c0 - k : 0;   // only unused lags clamp
-                        wx[(QB - k) % QB] = rx[col];
-                        wv[(QB - k) % QB] = rv[col];
-                    }
-                    for (int j0 = 0; j0 < 32; j0 += QB) {
-#pragma unroll
-                        for (int jj = 0; jj < QB; ++jj) {
-                            const int j = j0 + jj;
-                            wx[jj] = rx[c0 + j];
-                            wv[jj] = rv[c0 + j];
-                            const T uu = ur[j], vv = vr[j];
-#pragma unroll
-                            for (int k = 0; k < QB; ++k)
-                                af[k] = fma(wx[(jj - k + QB) % QB], uu, fma(wv[(jj - k + QB) % QB], vv, af[k]));
+        // phase K2: lag sums of this warp's strips, by stages of PC lag rows.
+        // Lag p and strip row m read tile row m + 2r - p, so the stage of lags
+        // p0 .. p0+PC-1 holds tile rows from 2r - p0 - PC + 1 (NX rows) of x
+        // (sb0) and v (sb1).  A lane owns one lag row p and QB consecutive lag
+        // columns q0..q0+QB-1; along each strip row the x and v windows slide
+        // through registers (one new shared load each per column).
+        const int nqb = (K + QB - 1) / QB;
+        if (!tmafail) {
+            if (lane == 0) fence_proxy_async();
+            for (int s = gw; s < cx.nstrips; s += TW) {
+                int c, row0, col0;
+                strip_of(s, c, row0, col0);
+                bool ok = true;
+                for (int st = 0; st < ns; ++st) {
+                    const int p0 = st * PC, t0 = 2 * r - p0 - PC + 1;
+                    if (lane == 0) {
+                        uint64_t *mb = &mbar[0];
+                        mbar_expect_tx(mb, 2 * bytes_s() + (st == 0 ? 2 * bytes_i() : 0u));
+                        box_s(sb0, bx, c, row0, col0, t0, mb);
+                        box_s(sb1, bv, c, row0, col0, t0, mb);
+                        if (st == 0) {
+                            box_i(t1, B_U, c, row0, col0, mb);
+                            box_i(t2, B_V, c, row0, col0, mb);
                         }
                     }
+                    if (!land(0)) { ok = false; break; }
+                    if (st == 0) {
+                        // pixels outside the image (ragged strips) must not contribute
+                        const int gj = col0 + lane;
+                        for (int m = 0; m < MR; ++m) {
+                            if (row0 + m >= H || gj >= W) {
+                                t1[m * 32 + lane] = T(0);
+                                t2[m * 32 + lane] = T(0);
+                            }
+                        }
+                        __syncwarp();
+                    }
+                    const int np = K - p0 < PC ? K - p0 : PC;
+                    const int units = np * nqb;
+                    for (int u = lane; u < units; u += 32) {
+                        const int p = p0 + u / nqb, q0 = (u % nqb) * QB;
+                        S acc[QB];
 #pragma unroll
-                    for (int k = 0; k < QB; ++k) acc[k] = Sc::addv(acc[k], af[k]);
+                        for (int k = 0; k < QB; ++k) acc[k] = Sc::zero();
+                        for (int m = 0; m < MR; ++m) {
+                            const int srow = m + p0 + PC - 1 - p;     // = tile row m + 2r - p, minus t0
+                            const T *rx = sb0 + srow * cx.BW + off;
+                            const T *rv = sb1 + srow * cx.BW + off;
+                            const T *ur = t1 + m * 32, *vr = t2 + m * 32;
+                            const int c0 = 2 * r - q0;       // column of lag q0 at j = 0
+                            T wx[QB], wv[QB], af[QB];
+#pragma unroll
+                            for (int k = 0; k < QB; ++k) af[k] = T(0);
+#pragma unroll
+                            for (int k = 1; k < QB; ++k) {
+                                const int col = c0 - k >= 0 ? c0 - k : 0;   // only unused lags clamp
+                                wx[(QB - k) % QB] = rx[col];
+                                wv[(QB - k) % QB] = rv[col];
+                            }
+                            for (int j0 = 0; j0 < 32; j0 += QB) {
+#pragma unroll
+                                for (int jj = 0; jj < QB; ++jj) {
+                                    const int j = j0 + jj;
+                                    wx[jj] = rx[c0 + j];
+                                    wv[jj] = rv[c0 + j];
+                                    const T uu = ur[j], vv = vr[j];
+#pragma unroll
+                                    for (int k = 0; k < QB; ++k)
+                                        af[k] = fma(wx[(jj - k + QB) % QB], uu, fma(wv[(jj - k + QB) % QB], vv, af[k]));
+                                }
+                            }
+#pragma unroll
+                            for (int k = 0; k < QB; ++k) acc[k] = Sc::addv(acc[k], af[k]);
+                        }
+#pragma unroll
+                        for (int k = 0; k < QB; ++k)
+                            if (q0 + k < K) zp[c * KK + p * K + q0 + k] = Sc::add(zp[c * KK + p * K + q0 + k], acc[k]);
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
                 }
-#pragma unroll
-                for (int k = 0; k < QB; ++k)
-                    if (q0 + k < K) zp[c * KK + p * K + q0 + k] = Sc::add(zp[c * KK + p * K + q0 + k], acc[k]);
+                if (!ok) break;
             }
-            __syncwarp();
         }
         if (!sync()) return 0.0;
         // phase K3: one warp per kernel entry sums the per-warp rows in a fixed
@@ -725,41 +963,53 @@ struct Eng {
         passes += 4;   // B v, B x and the two lag correlations
         if (!sync()) return 0.0;
         S s = Sc::zero();
-        for (int e = tid; e < CKK; e += blockDim.x) { const T zv = __ldcg(zout + e); s = Sc::addv(s, zv * zv); }
+        for (int e = tid; e < CKK; e += blockDim.x) {
+            const T zv = __ldcg(zout + e);
+            s = Sc::addv(s, zv * zv);
+        }
         return Sc::to_double(block_sum<T>(s, red));
     }
 
     // ------------------------------------------------------------ MAID
     // One upper iteration of Algorithm 2; every CTA runs the same control flow
-    // on identical reduction results.
+    // on identical reduction results.  x~(b_k) is imported into B_XK; the trial
+    // solutions go to B_XT.
     __device__ void maid(const Job<T> &jb)
     {
         MaidIn st = jb.maid;
-        T *b = jb.bio, *x = (T *)jb.x, *q = jb.q;
+        T *b = jb.bio;
         const int CKK = cx.C * cx.K * cx.K;
         long long passes = 0;
         int ll_iters = 0, cg_iters = 0, ll_capped = 0, cg_capped = 0, trials = 0, rounds = 0, accepted = 0;
         int stopped = st.eps_stop > 0.0 && st.eps <= st.eps_stop;   // stop rule of Sec. 4.2
         double loss = 0.0, gxn = 0.0, znorm = 0.0, psi = 0.0, gn = 0.0, res = 0.0;
+        if (!stopped) {
+            import_dense(jb.x, B_XK);
+            if (!sync()) stopped = 1;
+        }
         int j = st.max_bt;
         for (int round = 0; round < st.max_rounds && alive && !stopped; ++round, ++j) {
             rounds = round + 1;
             // InexactGradient(b_k, eps_k, delta_k)
-            ll_iters += lower_solve(b, x, x, st.eps, st.ll_max_iters, gn, passes);
+            ll_iters += lower_solve(b, B_XK, B_XK, st.eps, st.ll_max_iters, gn, passes);
             if (!sync()) break;
             if (gn > st.eps) ll_capped = 1;
             double l0 = 0.0, gx0 = 0.0;
-            upper_loss(b, x, l0, gx0, passes);
+            upper_loss(b, B_XK, l0, gx0, passes);
             if (!alive) break;
             int capped = 0;
-            cg_iters += cg(b, x, cx.G, q, st.delta, st.cg_max_iters, true, res, capped, passes);
+            cg_iters += cg(b, B_XK, B_G, st.delta, st.cg_max_iters, true, res, capped, passes);
             if (!alive) break;
             if (capped) cg_capped = 1;
             if (!sync()) break;
-            const double zz = cross(b, x, q, cx.ZK, true, true, passes);
+            const double zz = cross(b, B_XK, B_Q, cx.ZK, true, true, passes);
             if (!alive) break;
             znorm = sqrt(zz);
-            if (!isfinite(znorm)) { fail(ST_NONFINITE); break; }
+            if (!isfinite(znorm)) {
+                if (tid == 0) raise(ST_NONFINITE);
+                alive = false;
+                break;
+            }
             bool done = false;
             for (int i = 0; i < j; ++i) {
                 ++trials;
@@ -768,18 +1018,18 @@ struct Eng {
                     cx.BT[e] = (T)((double)__ldcg(b + e) - st.step * (double)__ldcg(cx.ZK + e));
                 if (!sync()) break;
                 double g1 = 0.0;
-                ll_iters += lower_solve(cx.BT, x, cx.XT, st.eps, st.ll_max_iters, g1, passes);
+                ll_iters += lower_solve(cx.BT, B_XK, B_XT, st.eps, st.ll_max_iters, g1, passes);
                 if (!sync()) break;
                 if (g1 > st.eps) ll_capped = 1;
                 double l1 = 0.0, gx1 = 0.0;
-                upper_loss(cx.BT, cx.XT, l1, gx1, passes);
+                upper_loss(cx.BT, B_XT, l1, gx1, passes);
                 if (!alive) break;
                 // psi of Eq. 3.4 with eps_bar = eps_k
                 const double eb = st.eps;
                 psi = l1 + gx1 * eb + 0.5 * st.L_gx * eb * eb - l0 + gx0 * eb + st.lambda * st.step * zz;
                 if (psi <= 0.0) {
                     for (long long e = gstart(); e < CKK; e += gstride()) b[e] = __ldcg(cx.BT + e);
-                    for (long long e = gstart(); e < cx.N; e += gstride()) x[e] = __ldcg(cx.XT + e);
+                    copy_buf(B_XK, -1, B_XT);
                     loss = l1;
                     gxn = gx1;
                     st.eps *= st.nu_up;
@@ -799,6 +1049,11 @@ struct Eng {
             st.delta *= st.nu_down;
             if (st.eps_stop > 0.0 && st.eps <= st.eps_stop) stopped = 1;
         }
+        // x~ and q back to the caller (x unchanged unless a step was accepted)
+        if (alive && rounds > 0 && sync()) {
+            if (accepted) export_dense(B_XK, (T *)jb.x);
+            export_dense(B_Q, jb.q);
+        }
         if (tid == 0 && blockIdx.x == 0) {
             DevOut *o = cx.out;
             o->accepted = accepted; o->rounds = rounds; o->trials = trials;
@@ -812,9 +1067,9 @@ struct Eng {
 
 template <typename T>
 __global__ void __launch_bounds__(MAXNW * 32, 1) adp_kernel(const __grid_constant__ Ctx<T> cx,
-                                                         const __grid_constant__ Job<T> jb)
+                                                            const __grid_constant__ Job<T> jb)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     using S = typename Scal<T>::S;
     __shared__ S red[MAXNW];
     __shared__ S bcast;
@@ -826,47 +1081,79 @@ __global__ void __launch_bounds__(MAXNW * 32, 1) adp_kernel(const __grid_constan
     const bool lead = threadIdx.x == 0 && blockIdx.x == 0;
     long long passes = 0;
     switch (jb.mode) {
-    case M_APPLY_B: e.apply(jb.b, jb.x, jb.xo, false); break;
-    case M_APPLY_BT: e.apply(jb.b, jb.x, jb.xo, true); break;
-    case M_GRAD_LOWER: e.grad_lower(jb.b, jb.x, jb.xo); break;
-    case M_HESS_VEC: e.load_weights(jb.b); e.hess_vec(jb.x, jb.v, jb.xo); break;
+    case M_IMPORT_Y: e.import_dense(jb.x, B_Y); break;
+    case M_APPLY_B:
+    case M_APPLY_BT:
+        e.import_dense(jb.x, B_IN1);
+        e.load_weights(jb.b);
+        if (e.sync()) e.apply(B_IN1, jb.xo, jb.mode == M_APPLY_BT);
+        break;
+    case M_GRAD_LOWER:
+        e.import_dense(jb.x, B_XK);
+        if (e.sync()) e.grad_lower(jb.b, B_XK, jb.xo);
+        break;
+    case M_HESS_VEC:
+        e.import_dense(jb.x, B_XK);
+        e.import_dense(jb.v, B_IN1);
+        e.load_weights(jb.b);
+        if (e.sync()) e.hess_vec(B_XK, B_IN1, B_HP, jb.xo);
+        break;
     case M_LOWER_SOLVE: {
+        if (jb.y) e.import_dense(jb.y, B_Y);
+        e.import_dense(jb.x, B_XK);
         double gn = 0.0;
-        const int it = e.lower_solve(jb.b, jb.x, jb.xo, jb.eps, jb.max_iters, gn, passes);
-        if (lead) { cx.out->iters = it; cx.out->gradnorm = gn; cx.out->capped = gn > jb.eps; cx.out->conv_passes = passes; }
+        int it = 0;
+        if (e.sync()) {
+            it = e.lower_solve(jb.b, B_XK, B_XK, jb.eps, jb.max_iters, gn, passes);
+            if (e.sync()) e.export_dense(B_XK, jb.xo);
+        }
+        if (lead) {
+            cx.out->iters = it; cx.out->gradnorm = gn; cx.out->capped = gn > jb.eps;
+            cx.out->conv_passes = passes;
+        }
         break;
     }
     case M_UPPER_LOSS: {
+        e.import_dense(jb.x, B_XK);
         double loss = 0.0, gxn = 0.0;
-        e.upper_loss(jb.b, jb.x, loss, gxn, passes);
-        if (e.alive && jb.xo) {
-            for (long long i = e.gstart(); i < cx.N; i += e.gstride()) jb.xo[i] = __ldcg(cx.G + i);
+        if (e.sync()) {
+            e.upper_loss(jb.b, B_XK, loss, gxn, passes);
+            if (e.alive && jb.xo) e.export_dense(B_G, jb.xo);
         }
         if (lead) { cx.out->loss = loss; cx.out->gradx_norm = gxn; cx.out->conv_passes = passes; }
         break;
     }
     case M_HYPERGRAD: {
         const bool given = jb.v != nullptr;
+        e.import_dense(jb.x, B_XK);
+        e.import_dense(jb.q, B_Q);
+        if (given) e.import_dense(jb.v, B_IN1);
+        if (!e.sync()) break;
         double gxn = 0.0, loss = 0.0;
-        const T *rhs = jb.v;
+        int rhs = B_IN1;
         if (!given) {
-            e.upper_loss(jb.b, jb.x, loss, gxn, passes);
+            e.upper_loss(jb.b, B_XK, loss, gxn, passes);
             if (!e.alive) break;
-            rhs = cx.G;
+            rhs = B_G;
         }
         double res = 0.0;
         int capped = 0;
-        const int it = e.cg(jb.b, jb.x, rhs, jb.q, jb.delta, jb.max_iters, false, res, capped, passes);
+        const int it = e.cg(jb.b, B_XK, rhs, jb.delta, jb.max_iters, false, res, capped, passes);
         if (!e.alive) break;
         if (!e.sync()) break;
-        const double zz = e.cross(jb.b, jb.x, jb.q, jb.z, true, !given, passes);
+        const double zz = e.cross(jb.b, B_XK, B_Q, jb.z, true, !given, passes);
+        if (e.alive) e.export_dense(B_Q, jb.q);
         if (lead) {
             cx.out->cg_iters = it; cx.out->resnorm = res; cx.out->capped = capped;
             cx.out->znorm = sqrt(zz); cx.out->conv_passes = passes;
         }
         break;
     }
-    case M_CROSS: e.cross(jb.b, jb.x, jb.v, jb.z, false, false, passes); break;
+    case M_CROSS:
+        e.import_dense(jb.x, B_XK);
+        e.import_dense(jb.v, B_IN1);
+        if (e.sync()) e.cross(jb.b, B_XK, B_IN1, jb.z, false, false, passes);
+        break;
     case M_MAID: e.maid(jb); break;
     case M_WAIT_SELFTEST:
         // diagnostic: CTA 0 never arrives, so every other CTA's bounded wait at
@@ -875,6 +1162,7 @@ __global__ void __launch_bounds__(MAXNW * 32, 1) adp_kernel(const __grid_constan
         break;
     default: break;
     }
+    e.drain();
     if (lead) cx.out->barriers = (int)e.epoch;
 }
 

@@ -8,7 +8,7 @@
 // allocate behind their back.  This entry point therefore takes its workspace
 // from one fixed, file-scope device array instead of adp_problem_create's
 // cudaMalloc'd buffers.  The caller still passes the inputs and the in/out
-// image.
+// image.  Padded images of at most ADP_NOALLOC_MAX_IMAGE_BYTES are supported.
 //
 // The array lives in this file; device code never names it.  Host code may not
 // use its name as an address (on the host it is only a stand-in), so the
@@ -33,16 +33,19 @@ using namespace adp;
 namespace {
 
 // Layout of the scratch array: barrier counter | status/result record |
-// reduction partials | five images (x_k, x_{k+1}, y_k, y_{k+1}, residual).
+// reduction partials | kernel weight slots | the padded images of a lower
+// solve (y, x_k, x_{k+1}, y_k, y_{k+1}, residual, solution).
 constexpr size_t kHeadBytes = 256;                                   // barrier counter
 constexpr size_t kOutBytes = 256;                                    // DevOut
 constexpr size_t kPartBytes = (size_t)NSLOT * GT_MAX * sizeof(double);
-constexpr size_t kImages = 5;
+constexpr size_t kWeightBytes = ADP_NOALLOC_WEIGHT_BYTES;
+constexpr size_t kImages = NBUF_LOWER;
 constexpr size_t kImageBytes = ADP_NOALLOC_MAX_IMAGE_BYTES;
-constexpr size_t kScratchBytes = kHeadBytes + kOutBytes + kPartBytes + kImages * kImageBytes;
+constexpr size_t kScratchBytes = kHeadBytes + kOutBytes + kPartBytes + kWeightBytes + kImages * kImageBytes;
 
 static_assert(sizeof(DevOut) <= kOutBytes, "result record does not fit its slot");
 static_assert(kScratchBytes == ADP_NOALLOC_SCRATCH_BYTES, "scratch layout and the size stated in adp.h differ");
+static_assert(kImages == 7, "adp.h states seven images");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -91,55 +94,72 @@ template <typename T>
 adp_status run_noalloc(const adp_params &q, DeviceSetup &ds, const void *y, const void *b, void *x, double eps,
                        int max_iters, cudaStream_t stream, int *iters, double *gradnorm)
 {
-    constexpr int MR = Cfg<T>::MR;
-    const int Kp = round_up(q.K, Cfg<T>::PC);
-    const int nx = (q.W + 31) / 32, ny = (q.H + MR - 1) / MR, nstrips = q.C * nx * ny;
-    int w_elems = 0, warp_elems = 0, total = 0, nw = MAXNW;
+    constexpr int MR = Cfg<T>::MR, NX = Cfg<T>::PC + MR - 1;
+    const Geom g = make_geom<T>(q.C, q.H, q.W, q.K);
+    const size_t img_bytes = (size_t)g.Np * sizeof(T);
+    if (img_bytes > kImageBytes) {
+        char msg[200];
+        snprintf(msg, sizeof msg,
+                 "padded image of %zu bytes exceeds the no-allocation limit of %zu bytes (C*(H+2*Gy)*Wp*element size)",
+                 img_bytes, (size_t)kImageBytes);
+        return fail(ADP_EINVAL, msg);
+    }
+    if ((size_t)4 * q.C * q.K * g.Kp * sizeof(T) > kWeightBytes)
+        return fail(ADP_EINVAL, "kernel weights exceed the no-allocation limit (4*C*K*Kp*element size)");
+    int total = 0, nw = MAXNW;
     for (; nw >= 1; --nw) {
-        smem_layout<T>(q.C, q.K, nw, w_elems, warp_elems, total);
-        if ((size_t)total * sizeof(T) + 5 * 1024 <= (size_t)ds.maxsmem) break;
+        total = Layout<T>(q.C, q.K, nw, g.wsm).total;
+        if ((size_t)total * sizeof(T) + 128 + 5 * 1024 <= (size_t)ds.maxsmem) break;
     }
     if (nw < 1) return fail(ADP_EINVAL, "kernel size too large for shared memory");
-    const size_t smem = (size_t)total * sizeof(T);
+    const size_t smem = (size_t)total * sizeof(T) + 128;   // + alignment slack of the TMA destinations
     const void *fn = sizeof(T) == 4 ? kernel_f32() : kernel_f64();
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * nw, smem) != cudaSuccess || occ < 1)
         return fail(ADP_ECUDA, "occupancy query failed");
-    long long grid = nstrips <= (long long)ds.nsm * nw ? (nstrips < ds.nsm ? nstrips : ds.nsm)
-                                                        : ((long long)nstrips + nw - 1) / nw;
+    long long grid = g.nstrips <= (long long)ds.nsm * nw ? (g.nstrips < ds.nsm ? g.nstrips : ds.nsm)
+                                                          : ((long long)g.nstrips + nw - 1) / nw;
     if (grid > (long long)occ * ds.nsm) grid = (long long)occ * ds.nsm;
     if (grid > GT_MAX) grid = GT_MAX;
 
     unsigned char *base = ds.scratch;
+    unsigned char *img = base + kHeadBytes + kOutBytes + kPartBytes + kWeightBytes;
     Ctx<T> c;
     memset(&c, 0, sizeof c);
-    c.C = q.C; c.H = q.H; c.W = q.W; c.K = q.K; c.r = (q.K - 1) / 2; c.Kp = Kp;
-    c.nx = nx; c.ny = ny; c.nstrips = nstrips;
-    c.PA = 32 + 2 * c.r; c.RA = MR + Kp - 1;
+    {
+        char emsg[200];
+        if (encode_tensor_maps(img, NBUF_LOWER, q.C, g, (int)sizeof(T), MR, NX, &c.map_s, &c.map_1, &c.map_i, emsg,
+                               sizeof emsg))
+            return fail(ADP_ECUDA, emsg);
+    }
+    c.C = q.C; c.H = q.H; c.W = q.W; c.K = q.K; c.r = g.r; c.Kp = g.Kp;
+    c.r4 = g.r4; c.Gx = g.Gx; c.Gy = g.Gy; c.Wp = g.Wp; c.Hp = g.Hp; c.BW = g.BW;
+    c.nx = g.nx; c.ny = g.ny; c.nstrips = g.nstrips; c.wsm = g.wsm; c.multiwrap = g.multiwrap;
+    c.N = g.N; c.HW = g.HW; c.HWp = g.HWp; c.Np = g.Np;
     c.trace = nullptr; c.trace_cap = 0;
-    c.HW = (long long)q.H * q.W; c.N = c.HW * q.C;
     c.reg = q.reg; c.alpha = q.alpha; c.rp = q.reg_param; c.beta = q.beta; c.w0 = q.sobolev_w0;
     c.ddphi_max = q.reg == ADP_REG_QUAD ? 1.0 : 1.0 / q.reg_param;
     c.alphaT = (T)q.alpha; c.rpT = (T)q.reg_param; c.irpT = (T)(1.0 / q.reg_param);
-    c.y = (const T *)y; c.a = nullptr;
+    c.a = nullptr;
     c.bar = (unsigned *)base;
     c.out = (DevOut *)(base + kHeadBytes);
     c.part = (double *)(base + kHeadBytes + kOutBytes);
-    T *img = (T *)(base + kHeadBytes + kOutBytes + kPartBytes);
-    const size_t stride = kImageBytes / sizeof(T);
-    c.X0 = img; c.X1 = img + stride; c.Y0 = img + 2 * stride; c.Y1 = img + 3 * stride; c.U = img + 4 * stride;
+    c.wg = (T *)(base + kHeadBytes + kOutBytes + kPartBytes);
+    c.ws = (T *)img;
     const double to = q.wait_timeout_s > 0 ? q.wait_timeout_s : 2.0;
     c.timeout_ns = (long long)(to * 1e9);
 
     Job<T> j;
     memset(&j, 0, sizeof j);
-    j.mode = M_LOWER_SOLVE; j.b = (const T *)b; j.x = (const T *)x; j.xo = (T *)x;
+    j.mode = M_LOWER_SOLVE; j.b = (const T *)b; j.x = (const T *)x; j.xo = (T *)x; j.y = (const T *)y;
     j.eps = eps; j.max_iters = max_iters;
 
-    // what must start at zero: the barrier's arrival counter and the record
-    // (its status word); the images are written before they are read
-    if (cudaMemsetAsync(base, 0, kHeadBytes + kOutBytes, stream) != cudaSuccess)
-        return fail(ADP_ECUDA, "clearing the scratch header failed");
+    // what must start at zero: the barrier's arrival counter, the record (its
+    // status word) and the images (their padding columns are read, never
+    // written); the weights are written before they are read
+    if (cudaMemsetAsync(base, 0, kHeadBytes + kOutBytes, stream) != cudaSuccess ||
+        cudaMemsetAsync(img, 0, NBUF_LOWER * img_bytes, stream) != cudaSuccess)
+        return fail(ADP_ECUDA, "clearing the scratch failed");
     void *args[] = {(void *)&c, (void *)&j};
     cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(32 * nw), args, smem, stream);
     if (e != cudaSuccess) return fail(ADP_ECUDA, cudaGetErrorString(e));
@@ -169,14 +189,6 @@ extern "C" adp_status adp_lower_solve_noalloc(const adp_params *params, const vo
     if (q.reg < 0 || q.reg > 2 || (q.reg != ADP_REG_QUAD && !(q.reg_param > 0)) || !(q.alpha >= 0))
         return fail(ADP_EINVAL, "bad regulariser parameters");
     if (max_iters < 0) return fail(ADP_EINVAL, "max_iters must be >= 0");
-    const size_t esize = q.prec == ADP_F32 ? sizeof(float) : sizeof(double);
-    const size_t bytes = (size_t)q.C * q.H * q.W * esize;
-    if (bytes > kImageBytes) {
-        char msg[160];
-        snprintf(msg, sizeof msg, "image of %zu bytes exceeds the no-allocation limit of %zu bytes (C*H*W*element size)",
-                 bytes, (size_t)kImageBytes);
-        return fail(ADP_EINVAL, msg);
-    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return fail(ADP_ECUDA, "cudaGetDevice failed");
     DeviceSetup *ds = nullptr;

@@ -44,6 +44,7 @@ OP_CASES = [
     (2, 33, 97, 15, adp.ADP_F32),
     (1, 40, 40, 1, adp.ADP_F32),      # K = 1
     (1, 8, 10, 9, adp.ADP_F32),       # kernel larger than the image: multiple wraps
+    (1, 12, 14, 31, adp.ADP_F32),     # halo wider than the image: ghosts hold several periods
     (1, 64, 80, 31, adp.ADP_F32),
     (3, 256, 256, 15, adp.ADP_F32),   # full size of the 256^2 RGB workload
     (1, 64, 64, 7, adp.ADP_F64),      # the 64^2 FP64 workload
