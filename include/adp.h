@@ -155,6 +155,51 @@ adp_status adp_maid_init(adp_problem *p, adp_maid_state *s);
  * s->accepted = 0 and b, x unchanged. */
 adp_status adp_maid_step(adp_problem *p, adp_maid_state *s, void *b, void *x, void *q);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent problems in one cooperative launch (uneven image sizes and
+ * kernel sizes; one precision and device).  The grid is split into one group
+ * of CTAs per problem; a group has its own barrier counter, reductions and
+ * result record, and runs that problem's program exactly as a launch of its
+ * own would (with fewer CTAs).  Group sizes start proportional to each
+ * problem's convolution work (strips x K^2) and, after every
+ * adp_batch_maid_step, are re-balanced from the measured time of each group
+ * (half the old estimate, half the measurement) so that the groups finish
+ * together; at most one group per co-resident CTA, and no group larger than
+ * the problem's own launch.  There is no counterpart in the paper: this is the
+ * batched form of adp_maid_step. */
+typedef struct adp_batch adp_batch;
+
+/* Groups n problems; they must outlive the batch.  Launches go to problem 0's
+ * stream.  Allocates small device tables (cudaMalloc).  ADP_EINVAL for a mix
+ * of precisions or devices, or more problems than co-resident CTAs. */
+adp_status adp_batch_create(adp_problem *const *ps, int n, adp_batch **out);
+void adp_batch_destroy(adp_batch *bt);
+
+/* One upper iteration of Algorithm 2 on every problem of the batch in one
+ * launch: st[i], b[i], x[i], q[i] are problem i's arguments of
+ * adp_maid_step.  Returns ADP_OK when every problem accepted a step or has
+ * stopped; otherwise the first failure (ADP_ELSFAIL when a problem exhausted
+ * its backtracking rounds: its st[i] reports the shrunk eps, delta, step). */
+adp_status adp_batch_maid_step(adp_batch *bt, adp_maid_state *st, void *const *b, void *const *x,
+                               void *const *q);
+
+/* A device-resident MAID run: max_steps batched upper iterations captured
+ * once into a CUDA graph and replayed with no host round trip.  The MAID
+ * state of every problem stays on the device between steps; a problem stops
+ * for good at the stop rule (eps <= eps_stop) or when a step exhausts its
+ * rounds, and its later steps return at once.  st[i] receives the final
+ * eps, delta, step, k, the report of the last launch and `stopped`; totals
+ * (optional, 4 values per problem) the run's FISTA + CG iterations,
+ * convolution passes, upper iterations that ran, and accepted steps.  The
+ * partition is the batch's current one. */
+adp_status adp_batch_maid_run_graph(adp_batch *bt, adp_maid_state *st, void *const *b, void *const *x,
+                                    void *const *q, int max_steps, long long *totals);
+
+/* CTAs of problem i's group in the next launch; device time (ms) of the last
+ * batched launch (adp_batch_maid_step) or graph (adp_batch_maid_run_graph). */
+int adp_batch_group_size(adp_batch *bt, int i);
+double adp_batch_last_kernel_ms(adp_batch *bt);
+
 /* Diagnostics of the last call on p: number of full-image convolution passes
  * it executed (each is 2 K^2 C H W flops; the kernel-gradient correlation
  * counts as two), and the number of CTAs of its cooperative launch. */

@@ -29,8 +29,9 @@ EXPORTS = ("adp_problem_create", "adp_problem_destroy", "adp_apply_B", "adp_appl
            "adp_grad_lower", "adp_hess_vec", "adp_lower_solve", "adp_upper_loss", "adp_hypergrad",
            "adp_cross_t", "adp_maid_init", "adp_maid_step", "adp_conv_passes_last",
            "adp_grid_size", "adp_warps_per_cta", "adp_last_kernel_ms", "adp_trace_enable",
-           "adp_trace_read", "adp_lower_solve_noalloc", "adp_selftest_wait_timeout", "adp_last_error",
-           "adp_status_string")
+           "adp_trace_read", "adp_lower_solve_noalloc", "adp_selftest_wait_timeout", "adp_batch_create",
+           "adp_batch_destroy", "adp_batch_maid_step", "adp_batch_maid_run_graph", "adp_batch_group_size",
+           "adp_batch_last_kernel_ms", "adp_last_error", "adp_status_string")
 
 
 class AdpError(RuntimeError):
@@ -94,6 +95,15 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
             "adp_trace_read": (i, [P, ct.POINTER(ct.c_longlong), i]),
             "adp_lower_solve_noalloc": (i, [ct.POINTER(adp_params), vp, vp, vp, d, i, vp, ip, dp]),
             "adp_selftest_wait_timeout": (i, [P]),
+            "adp_batch_create": (i, [ct.POINTER(ct.c_void_p), i, ct.POINTER(ct.c_void_p)]),
+            "adp_batch_destroy": (None, [P]),
+            "adp_batch_maid_step": (i, [P, ct.POINTER(adp_maid_state), ct.POINTER(ct.c_void_p),
+                                        ct.POINTER(ct.c_void_p), ct.POINTER(ct.c_void_p)]),
+            "adp_batch_maid_run_graph": (i, [P, ct.POINTER(adp_maid_state), ct.POINTER(ct.c_void_p),
+                                             ct.POINTER(ct.c_void_p), ct.POINTER(ct.c_void_p), i,
+                                             ct.POINTER(ct.c_longlong)]),
+            "adp_batch_group_size": (i, [P, i]),
+            "adp_batch_last_kernel_ms": (ct.c_double, [P]),
             "adp_last_error": (ct.c_char_p, []),
             "adp_status_string": (ct.c_char_p, [i]),
         }
@@ -334,6 +344,67 @@ def adp_lower_solve_noalloc(params: Params, y, b, x, eps, max_iters=300, stream=
                                             float(eps), int(max_iters), ct.c_void_p(s.cuda_stream),
                                             ct.byref(it), ct.byref(gn)), ok=(ADP_OK, ADP_ENOCONV))
     return it.value, gn.value, st == ADP_ENOCONV
+
+
+# ----------------------------------------------------------------- batches
+class Batch:
+    """Many problems in one cooperative launch (adp_batch_*): one MAID upper
+    iteration of every problem per launch, or a whole device-resident run
+    replayed from a CUDA graph.  The problems must outlive the batch."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        self.lib = load_library()
+        self.n = len(self.problems)
+        arr = (ct.c_void_p * self.n)(*[p.handle for p in self.problems])
+        h = ct.c_void_p()
+        with torch.cuda.device(self.problems[0].device):
+            _check(self.lib.adp_batch_create(arr, self.n, ct.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle is not None:
+            self.lib.adp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _arrays(self, states, bs, xs, qs):
+        st = (adp_maid_state * self.n)(*states)
+        pb = (ct.c_void_p * self.n)(*[p._k(b, "b").value for p, b in zip(self.problems, bs)])
+        px = (ct.c_void_p * self.n)(*[p._i(x, "x").value for p, x in zip(self.problems, xs)])
+        pq = (ct.c_void_p * self.n)(*[p._i(q, "q").value for p, q in zip(self.problems, qs)])
+        return st, pb, px, pq
+
+    def maid_step(self, states, bs, xs, qs):
+        """One upper iteration on every problem (in place); states are updated.
+        Returns the list of accepted flags."""
+        st, pb, px, pq = self._arrays(states, bs, xs, qs)
+        _check(self.lib.adp_batch_maid_step(self.handle, st, pb, px, pq), ok=(ADP_OK, ADP_ELSFAIL))
+        for i in range(self.n):
+            ct.memmove(ct.byref(states[i]), ct.byref(st[i]), ct.sizeof(adp_maid_state))
+        return [bool(s.accepted) for s in states]
+
+    def maid_run_graph(self, states, bs, xs, qs, max_steps):
+        """Up to max_steps upper iterations on every problem from one CUDA
+        graph (state kept on the device).  Returns per-problem totals
+        (fused iterations, convolution passes, upper iterations, accepted)."""
+        st, pb, px, pq = self._arrays(states, bs, xs, qs)
+        tot = (ct.c_longlong * (4 * self.n))()
+        _check(self.lib.adp_batch_maid_run_graph(self.handle, st, pb, px, pq, int(max_steps), tot))
+        for i in range(self.n):
+            ct.memmove(ct.byref(states[i]), ct.byref(st[i]), ct.sizeof(adp_maid_state))
+        return [tuple(tot[4 * i: 4 * i + 4]) for i in range(self.n)]
+
+    def group_sizes(self):
+        return [int(self.lib.adp_batch_group_size(self.handle, i)) for i in range(self.n)]
+
+    def last_kernel_ms(self) -> float:
+        return float(self.lib.adp_batch_last_kernel_ms(self.handle))
 
 
 # ----------------------------------------------------------------- autograd

@@ -18,14 +18,18 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <type_traits>
+#include <vector>
 
 using namespace adp;
 
 namespace adp {
 const void *kernel_f32();
 const void *kernel_f64();
+const void *kernel_f32_batched();
+const void *kernel_f64_batched();
 } // namespace adp
 
 static thread_local char g_err[512];
@@ -447,7 +451,7 @@ adp_status adp_maid_step(adp_problem *p, adp_maid_state *s, void *b, void *x, vo
     mi.eps = s->eps; mi.delta = s->delta; mi.step = s->step; mi.lambda = s->lambda;
     mi.rho_up = s->rho_up; mi.rho_down = s->rho_down; mi.nu_up = s->nu_up; mi.nu_down = s->nu_down;
     mi.L_gx = s->L_gx; mi.eps_stop = s->eps_stop; mi.max_bt = s->max_bt; mi.max_rounds = s->max_rounds;
-    mi.ll_max_iters = s->ll_max_iters; mi.cg_max_iters = s->cg_max_iters; mi.k = s->k;
+    mi.ll_max_iters = s->ll_max_iters; mi.cg_max_iters = s->cg_max_iters; mi.k = s->k; mi.halted = 0;
     adp_status st = dispatch_job(p, M_MAID, nullptr, x, nullptr, nullptr, q, nullptr, b, 0, 0, 0, &mi);
     if (st != ADP_OK) return st;
     const DevOut *o = p->hout;
@@ -496,6 +500,367 @@ int adp_trace_read(adp_problem *p, long long *host_out, int cap)
     if (n > 0 && cudaMemcpy(host_out, p->trace, (size_t)2 * n * sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess)
         return -1;
     return n;
+}
+
+} // extern "C"
+
+// ------------------------------------------------------------ batched MAID
+struct adp_batch {
+    std::vector<adp_problem *> ps;
+    int n, prec, nw;
+    size_t esize, ctx_bytes, job_bytes, smem;
+    int max_ctas;              // co-resident CTAs of the batched kernel
+    std::vector<int> first;    // group g = CTAs first[g] .. first[g+1]-1
+    std::vector<double> work;  // balancer: estimated CTA-time of each problem's step
+    void *dctx, *djob;         // launch records (device), n each
+    int *dfirst;
+    unsigned *dbar;            // one barrier counter per problem (256-byte stride)
+    DevOut *dout, *hout;       // one result record per problem
+    MaidTotals *dtot;          // running totals (graph runs)
+    unsigned char *hctx, *hjob;   // pinned staging of the launch records
+    cudaEvent_t ev0, ev1;
+    float last_ms;
+};
+
+static const size_t kBarStride = 64;   // unsigned counters, 256 bytes apart
+
+static void batch_free(adp_batch *bt)
+{
+    if (!bt) return;
+    void *dev[] = {bt->dctx, bt->djob, bt->dfirst, bt->dbar, bt->dout, bt->dtot};
+    for (void *q : dev) if (q) cudaFree(q);
+    if (bt->hout) cudaFreeHost(bt->hout);
+    if (bt->hctx) cudaFreeHost(bt->hctx);
+    if (bt->hjob) cudaFreeHost(bt->hjob);
+    if (bt->ev0) cudaEventDestroy(bt->ev0);
+    if (bt->ev1) cudaEventDestroy(bt->ev1);
+    delete bt;
+}
+
+// group sizes proportional to the work estimates, at least one CTA each and at
+// most the problem's own grid (its reduction and gradient buffers are sized
+// for that), summing to at most max_ctas
+static void batch_partition(adp_batch *bt)
+{
+    const int n = bt->n;
+    double tot = 0.0;
+    for (int i = 0; i < n; ++i) tot += bt->work[i];
+    std::vector<int> g(n);
+    int sum = 0;
+    for (int i = 0; i < n; ++i) {
+        int gi = (int)(bt->max_ctas * bt->work[i] / tot);
+        gi = std::max(1, std::min(gi, bt->ps[i]->grid));
+        g[i] = gi;
+        sum += gi;
+    }
+    // hand out the remainder to the problems with the most work per CTA
+    while (sum < bt->max_ctas) {
+        int best = -1;
+        double bw = 0.0;
+        for (int i = 0; i < n; ++i)
+            if (g[i] < bt->ps[i]->grid && bt->work[i] / g[i] > bw) { bw = bt->work[i] / g[i]; best = i; }
+        if (best < 0) break;
+        ++g[best];
+        ++sum;
+    }
+    while (sum > bt->max_ctas) {   // only when rounding overshot: take from the least loaded
+        int best = -1;
+        double bw = 1e300;
+        for (int i = 0; i < n; ++i)
+            if (g[i] > 1 && bt->work[i] / g[i] < bw) { bw = bt->work[i] / g[i]; best = i; }
+        if (best < 0) break;
+        --g[best];
+        --sum;
+    }
+    bt->first.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) bt->first[i + 1] = bt->first[i] + g[i];
+}
+
+template <typename T>
+static void batch_fill(adp_batch *bt, const adp_maid_state *st, void *const *b, void *const *x, void *const *q,
+                       bool resident)
+{
+    for (int i = 0; i < bt->n; ++i) {
+        adp_problem *p = bt->ps[i];
+        Ctx<T> c = make_ctx<T>(p);
+        c.bar = bt->dbar + i * kBarStride;
+        c.out = bt->dout + i;
+        c.totals = resident ? bt->dtot + i : nullptr;
+        c.trace = nullptr;
+        c.trace_cap = 0;
+        memcpy(bt->hctx + i * bt->ctx_bytes, &c, sizeof c);
+        Job<T> j;
+        memset(&j, 0, sizeof j);
+        j.mode = M_MAID;
+        j.x = (const T *)x[i];
+        j.q = (T *)q[i];
+        j.bio = (T *)b[i];
+        const adp_maid_state *s = st + i;
+        MaidIn &mi = j.maid;
+        mi.eps = s->eps; mi.delta = s->delta; mi.step = s->step; mi.lambda = s->lambda;
+        mi.rho_up = s->rho_up; mi.rho_down = s->rho_down; mi.nu_up = s->nu_up; mi.nu_down = s->nu_down;
+        mi.L_gx = s->L_gx; mi.eps_stop = s->eps_stop; mi.max_bt = s->max_bt; mi.max_rounds = s->max_rounds;
+        mi.ll_max_iters = s->ll_max_iters; mi.cg_max_iters = s->cg_max_iters; mi.k = s->k; mi.halted = 0;
+        j.maid_home = resident ? (MaidIn *)((unsigned char *)bt->djob + i * bt->job_bytes + offsetof(Job<T>, maid))
+                               : nullptr;
+        memcpy(bt->hjob + i * bt->job_bytes, &j, sizeof j);
+    }
+}
+
+// records of problem i after a launch: report into st[i] (and the state, from
+// the result record or, for device-resident runs, from the job's MAID state)
+static adp_status batch_report(adp_batch *bt, adp_maid_state *st, const MaidIn *resident_state)
+{
+    adp_status first_bad = ADP_OK;
+    for (int i = 0; i < bt->n; ++i) {
+        const DevOut *o = bt->hout + i;
+        adp_maid_state *s = st + i;
+        if (o->status == ST_TIMEOUT && first_bad == ADP_OK) first_bad = set_err(ADP_ETIMEOUT, "device-side wait gave up%s", "", 0);
+        if (o->status == ST_NONFINITE && first_bad == ADP_OK) first_bad = set_err(ADP_ENONFINITE, "non-finite value in a reduction%s", "", 0);
+        if (o->status != ST_OK) continue;
+        if (resident_state) {
+            const MaidIn &m = resident_state[i];
+            s->eps = m.eps; s->delta = m.delta; s->step = m.step; s->k = m.k;
+        } else if (o->rounds > 0 || o->stopped) {
+            s->eps = o->eps; s->delta = o->delta; s->step = o->step; s->k = o->k;
+        }
+        s->accepted = o->accepted; s->rounds = o->rounds; s->trials = o->trials;
+        s->ll_iters = o->ll_iters; s->cg_iters = o->cg_iters; s->ll_capped = o->ll_capped; s->cg_capped = o->cg_capped;
+        s->loss = o->loss; s->gradx_norm = o->gradx_norm; s->znorm = o->znorm; s->psi = o->psi;
+        s->stopped = o->stopped;
+        if (!resident_state && !o->accepted && !o->stopped && first_bad == ADP_OK)
+            first_bad = set_err(ADP_ELSFAIL, "MAID backtracking rounds exhausted for problem %s%lld", "", i);
+    }
+    return first_bad;
+}
+
+static adp_status batch_launch(adp_batch *bt, cudaStream_t stream)
+{
+    const void *fn = bt->prec == ADP_F32 ? kernel_f32_batched() : kernel_f64_batched();
+    void *ctxp = bt->dctx, *jobp = bt->djob;
+    int *fp = bt->dfirst;
+    int n = bt->n;
+    void *args[] = {&ctxp, &jobp, &fp, &n};
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3((unsigned)bt->first[n]);
+    cfg.blockDim = dim3(32 * bt->nw);
+    cfg.dynamicSmemBytes = bt->smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeCooperative;
+    attr.val.cooperative = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    CK(cudaMemsetAsync(bt->dbar, 0, (size_t)bt->n * kBarStride * sizeof(unsigned), stream));
+    CK(cudaMemsetAsync(bt->dout, 0, (size_t)bt->n * sizeof(DevOut), stream));
+    CK(cudaLaunchKernelExC(&cfg, fn, args));
+    return ADP_OK;
+}
+
+extern "C" {
+
+adp_status adp_batch_create(adp_problem *const *ps, int n, adp_batch **out)
+{
+    if (!ps || !out || n < 1) return set_err(ADP_EINVAL, "invalid batch%s", "", 0);
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!ps[i]) return set_err(ADP_EINVAL, "null problem in batch at %s%lld", "", i);
+        if (ps[i]->prm.prec != ps[0]->prm.prec || ps[i]->device != ps[0]->device)
+            return set_err(ADP_EINVAL, "batched problems must share precision and device%s", "", 0);
+    }
+    adp_batch *bt = new adp_batch();
+    bt->ps.assign(ps, ps + n);
+    bt->n = n;
+    bt->prec = ps[0]->prm.prec;
+    bt->esize = ps[0]->esize;
+    bt->ctx_bytes = bt->prec == ADP_F32 ? sizeof(Ctx<float>) : sizeof(Ctx<double>);
+    bt->job_bytes = bt->prec == ADP_F32 ? sizeof(Job<float>) : sizeof(Job<double>);
+    // one block shape for all: the fewest warps any problem allows, and the
+    // largest shared-memory footprint at that width
+    int nw = MAXNW;
+    for (adp_problem *p : bt->ps) nw = std::min(nw, p->nw);
+    bt->nw = nw;
+    size_t smem = 0;
+    for (adp_problem *p : bt->ps) {
+        const Geom &g = p->g;
+        const int tot = bt->prec == ADP_F32 ? Layout<float>(p->prm.C, p->prm.K, nw, g.wsm).total
+                                            : Layout<double>(p->prm.C, p->prm.K, nw, g.wsm).total;
+        smem = std::max(smem, (size_t)tot * bt->esize + 128);
+    }
+    bt->smem = smem;
+    adp_status st = ADP_OK;
+#define CKB(call)                                                                            \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            st = set_err(e_ == cudaErrorMemoryAllocation ? ADP_ENOMEM : ADP_ECUDA, "%s (code %lld)", \
+                         cudaGetErrorString(e_), (long long)e_);                             \
+            batch_free(bt);                                                                  \
+            return st;                                                                       \
+        }                                                                                    \
+    } while (0)
+    CKB(cudaSetDevice(ps[0]->device));
+    int nsm = 0, maxsmem = 0;
+    CKB(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ps[0]->device));
+    CKB(cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ps[0]->device));
+    const void *fn = bt->prec == ADP_F32 ? kernel_f32_batched() : kernel_f64_batched();
+    CKB(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem - 5 * 1024));
+    int occ = 0;
+    CKB(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * nw, smem));
+    bt->max_ctas = occ * nsm;
+    if (bt->max_ctas < n) {
+        batch_free(bt);
+        return set_err(ADP_EINVAL, "a batch holds at most one problem per co-resident CTA (%s%lld)", "", occ * nsm);
+    }
+    long long cap = 0;
+    for (adp_problem *p : bt->ps) cap += p->grid;
+    if (cap < bt->max_ctas) bt->max_ctas = (int)cap;
+    bt->work.resize(n);
+    for (int i = 0; i < n; ++i) bt->work[i] = (double)ps[i]->g.nstrips * ps[i]->prm.K * ps[i]->prm.K;
+    batch_partition(bt);
+    CKB(cudaMalloc(&bt->dctx, n * bt->ctx_bytes));
+    CKB(cudaMalloc(&bt->djob, n * bt->job_bytes));
+    CKB(cudaMalloc((void **)&bt->dfirst, (n + 1) * sizeof(int)));
+    CKB(cudaMalloc((void **)&bt->dbar, (size_t)n * kBarStride * sizeof(unsigned)));
+    CKB(cudaMalloc((void **)&bt->dout, (size_t)n * sizeof(DevOut)));
+    CKB(cudaMalloc((void **)&bt->dtot, (size_t)n * sizeof(MaidTotals)));
+    CKB(cudaMallocHost((void **)&bt->hout, (size_t)n * sizeof(DevOut)));
+    CKB(cudaMallocHost((void **)&bt->hctx, n * bt->ctx_bytes));
+    CKB(cudaMallocHost((void **)&bt->hjob, n * bt->job_bytes));
+    CKB(cudaEventCreate(&bt->ev0));
+    CKB(cudaEventCreate(&bt->ev1));
+#undef CKB
+    *out = bt;
+    return ADP_OK;
+}
+
+void adp_batch_destroy(adp_batch *bt)
+{
+    if (!bt) return;
+    cudaSetDevice(bt->ps[0]->device);
+    cudaStreamSynchronize(bt->ps[0]->stream);
+    batch_free(bt);
+}
+
+int adp_batch_group_size(adp_batch *bt, int i)
+{
+    if (!bt || i < 0 || i >= bt->n) return -1;
+    return bt->first[i + 1] - bt->first[i];
+}
+
+double adp_batch_last_kernel_ms(adp_batch *bt) { return bt ? (double)bt->last_ms : -1.0; }
+
+adp_status adp_batch_maid_step(adp_batch *bt, adp_maid_state *st, void *const *b, void *const *x, void *const *q)
+{
+    if (!bt || !st || !b || !x || !q) return set_err(ADP_EINVAL, "null argument%s", "", 0);
+    for (int i = 0; i < bt->n; ++i) {
+        if (!b[i] || !x[i] || !q[i]) return set_err(ADP_EINVAL, "null data pointer for problem %s%lld", "", i);
+        if (st[i].max_bt < 1 || st[i].max_rounds < 1 || st[i].ll_max_iters < 0 || st[i].cg_max_iters < 0)
+            return set_err(ADP_EINVAL, "invalid MAID state for problem %s%lld", "", i);
+    }
+    cudaStream_t stream = bt->ps[0]->stream;
+    CK(cudaSetDevice(bt->ps[0]->device));
+    if (bt->prec == ADP_F32) batch_fill<float>(bt, st, b, x, q, false);
+    else batch_fill<double>(bt, st, b, x, q, false);
+    CK(cudaMemcpyAsync(bt->dctx, bt->hctx, bt->n * bt->ctx_bytes, cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(bt->djob, bt->hjob, bt->n * bt->job_bytes, cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(bt->dfirst, bt->first.data(), (bt->n + 1) * sizeof(int), cudaMemcpyHostToDevice, stream));
+    CK(cudaEventRecord(bt->ev0, stream));
+    adp_status ls = batch_launch(bt, stream);
+    if (ls != ADP_OK) return ls;
+    CK(cudaEventRecord(bt->ev1, stream));
+    CK(cudaMemcpyAsync(bt->hout, bt->dout, bt->n * sizeof(DevOut), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    CK(cudaEventElapsedTime(&bt->last_ms, bt->ev0, bt->ev1));
+    const adp_status rs = batch_report(bt, st, nullptr);
+    // balancer: a group's CTA-time is its work estimate for the next step
+    bool any = false;
+    std::vector<double> w(bt->n);
+    for (int i = 0; i < bt->n; ++i) {
+        const double t = (double)(bt->hout[i].t_end - bt->hout[i].t_start);
+        const int gsz = bt->first[i + 1] - bt->first[i];
+        w[i] = t > 0 ? t * gsz : 0.0;
+        if (w[i] > 0) any = true;
+    }
+    if (any) {
+        double mn = 1e300, sw = 0.0, so = 0.0;
+        for (int i = 0; i < bt->n; ++i) if (w[i] > 0) mn = std::min(mn, w[i]);
+        for (int i = 0; i < bt->n; ++i) {
+            if (w[i] <= 0) w[i] = mn;
+            sw += w[i];
+            so += bt->work[i];
+        }
+        // half the old estimate, half the measurement (both normalised)
+        for (int i = 0; i < bt->n; ++i) bt->work[i] = 0.5 * bt->work[i] / so + 0.5 * w[i] / sw;
+        batch_partition(bt);
+    }
+    return rs;
+}
+
+adp_status adp_batch_maid_run_graph(adp_batch *bt, adp_maid_state *st, void *const *b, void *const *x,
+                                    void *const *q, int max_steps, long long *totals)
+{
+    if (!bt || !st || !b || !x || !q || max_steps < 1) return set_err(ADP_EINVAL, "invalid argument%s", "", 0);
+    for (int i = 0; i < bt->n; ++i)
+        if (!b[i] || !x[i] || !q[i]) return set_err(ADP_EINVAL, "null data pointer for problem %s%lld", "", i);
+    cudaStream_t stream = bt->ps[0]->stream;
+    CK(cudaSetDevice(bt->ps[0]->device));
+    if (bt->prec == ADP_F32) batch_fill<float>(bt, st, b, x, q, true);
+    else batch_fill<double>(bt, st, b, x, q, true);
+    CK(cudaMemcpyAsync(bt->dctx, bt->hctx, bt->n * bt->ctx_bytes, cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(bt->djob, bt->hjob, bt->n * bt->job_bytes, cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(bt->dfirst, bt->first.data(), (bt->n + 1) * sizeof(int), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemsetAsync(bt->dtot, 0, bt->n * sizeof(MaidTotals), stream));
+    CK(cudaStreamSynchronize(stream));
+    // capture the steps on a private stream (the legacy default stream cannot be captured)
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    adp_status res = ADP_OK;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int s = 0; s < max_steps && res == ADP_OK; ++s) res = batch_launch(bt, cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (res == ADP_OK && e2 != cudaSuccess) res = set_err(ADP_ECUDA, "graph capture: %s%lld", cudaGetErrorString(e2), 0);
+    } else {
+        res = set_err(ADP_ECUDA, "graph capture: %s%lld", cudaGetErrorString(e), 0);
+    }
+    if (res == ADP_OK) {
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) res = set_err(ADP_ECUDA, "graph instantiation: %s%lld", cudaGetErrorString(e), 0);
+    }
+    if (res == ADP_OK) {
+        cudaEventRecord(bt->ev0, cs);
+        e = cudaGraphLaunch(exec, cs);
+        cudaEventRecord(bt->ev1, cs);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) res = set_err(ADP_ECUDA, "graph launch: %s%lld", cudaGetErrorString(e), 0);
+        else cudaEventElapsedTime(&bt->last_ms, bt->ev0, bt->ev1);
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (res != ADP_OK) return res;
+    CK(cudaMemcpy(bt->hout, bt->dout, bt->n * sizeof(DevOut), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(bt->hjob, bt->djob, bt->n * bt->job_bytes, cudaMemcpyDeviceToHost));
+    std::vector<MaidIn> state(bt->n);
+    for (int i = 0; i < bt->n; ++i)
+        memcpy(&state[i], bt->hjob + i * bt->job_bytes + (bt->prec == ADP_F32 ? offsetof(Job<float>, maid) : offsetof(Job<double>, maid)), sizeof(MaidIn));
+    if (totals) {
+        std::vector<MaidTotals> t(bt->n);
+        CK(cudaMemcpy(t.data(), bt->dtot, bt->n * sizeof(MaidTotals), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < bt->n; ++i) {
+            totals[4 * i] = t[i].fused_iters; totals[4 * i + 1] = t[i].conv_passes;
+            totals[4 * i + 2] = t[i].upper_iters; totals[4 * i + 3] = t[i].accepted;
+        }
+    }
+    adp_status rs = batch_report(bt, st, state.data());
+    for (int i = 0; i < bt->n; ++i) {
+        st[i].stopped = (st[i].eps_stop > 0 && st[i].eps <= st[i].eps_stop) || state[i].halted;
+    }
+    return rs;
 }
 
 } // extern "C"

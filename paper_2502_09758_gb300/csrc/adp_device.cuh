@@ -35,6 +35,7 @@ struct DevOut {
     double eps, delta, step;
     long long conv_passes;       // number of full-image convolution passes executed
     int barriers, stopped;       // grid barriers executed by CTA 0; MAID stop rule fired
+    long long t_start, t_end;    // global timer (ns) at the program's start and end in CTA 0
 };
 
 __host__ __device__ constexpr int round_up(int a, int m) { return (a + m - 1) / m * m; }
@@ -71,18 +72,19 @@ __device__ __forceinline__ int ld_volatile_i32(const int *p)
 
 // Grid-wide barrier for a cooperative launch.  Thread 0 of each CTA adds one
 // to a monotonic arrival counter with release semantics and spins (acquire)
-// until the counter reaches epoch * gridDim.x; the CTA's other threads are
+// until the counter reaches epoch * nblk (the CTAs sharing the counter: the
+// whole grid, or one problem's group in a batched launch); the CTA's other threads are
 // ordered by bar.sync on both sides.  The host zeroes the counter before each
 // launch.  Every spin is bounded: after timeout_ns, or as soon as a CTA has
 // raised a status, the waiter records ST_TIMEOUT (unless something else was
 // recorded) and returns false, and the caller unwinds.
-__device__ __forceinline__ bool grid_sync(unsigned *count, unsigned epoch, int *status, long long timeout_ns,
-                                          int *s_flag)
+__device__ __forceinline__ bool grid_sync(unsigned *count, unsigned epoch, unsigned nblk, int *status,
+                                          long long timeout_ns, int *s_flag)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned target = epoch * gridDim.x;
+        const unsigned target = epoch * nblk;
         red_release_add_u32(count, 1u);
         const uint64_t t0 = globaltimer_ns();
         unsigned spins = 0;
@@ -469,6 +471,15 @@ enum Mode : int {
 struct MaidIn {
     double eps, delta, step, lambda, rho_up, rho_down, nu_up, nu_down, L_gx, eps_stop;
     int max_bt, max_rounds, ll_max_iters, cg_max_iters, k;
+    int halted;       // device-resident runs: a step exhausted its rounds, later steps do nothing
+};
+
+// Running totals of a device-resident MAID run (not cleared between launches).
+struct MaidTotals {
+    long long fused_iters;   // FISTA + CG iterations
+    long long conv_passes;
+    long long upper_iters;   // steps that ran (stop rule not yet fired)
+    long long accepted;
 };
 
 // Workspace buffers: one padded image each (see Ctx).  The first NBUF_LOWER
@@ -518,6 +529,7 @@ struct Ctx {
     double *zpart;                     // (grid * warps) x C*K*K
     unsigned *bar;                     // barrier arrival counter
     DevOut *out;
+    MaidTotals *totals;                // optional running totals (device-resident runs)
     long long timeout_ns;
 };
 
@@ -532,6 +544,7 @@ struct Job {
     T *z;             // kernel output
     T *bio;           // MAID: kernel in/out
     const T *y;       // data to import first (allocation-free lower solve), or null
+    MaidIn *maid_home; // MAID: where the updated state is written back (device-resident runs), or null
     double eps, delta;
     int max_iters, flag;
     MaidIn maid;

@@ -57,21 +57,22 @@ struct Eng {
     T *tau;                        // per-channel FISTA step 1/L_c
     int *sflag;
     int lane, warp, tid, nw, gw, TW, off, ns;
+    int nblk, bid;                 // CTAs sharing this program (grid or group) and this CTA's rank
     unsigned epoch;                // barriers passed so far (same in every thread)
     bool alive;                    // false once a grid barrier failed (uniform in the CTA)
     bool tmafail;                  // this warp gave up waiting for a TMA copy
 
-    __device__ Eng(const Ctx<T> &c, unsigned char *smem, S *red_, S *bcast_, double *redd_, T *tau_, S *gbuf_,
-                   int *sflag_)
+    __device__ Eng(const Ctx<T> &c, int nblk_, int bid_, unsigned char *smem, S *red_, S *bcast_, double *redd_,
+                   T *tau_, S *gbuf_, int *sflag_)
         : cx(c), mph(0), wslot(1), red(red_), bcast(bcast_), gbuf(gbuf_), redd(redd_), tau(tau_), sflag(sflag_),
-          epoch(0), alive(true), tmafail(false)
+          nblk(nblk_), bid(bid_), epoch(0), alive(true), tmafail(false)
     {
         lane = threadIdx.x & 31;
         warp = threadIdx.x >> 5;
         tid = threadIdx.x;
         nw = blockDim.x >> 5;
-        gw = warp * gridDim.x + blockIdx.x;
-        TW = gridDim.x * nw;
+        gw = warp * nblk + bid;
+        TW = nblk * nw;
         const Layout<T> L(cx.C, cx.K, nw, cx.wsm);
         // TMA destinations: 128-byte aligned (the host adds 128 bytes of slack)
         T *base = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem) + 127) & ~(uintptr_t)127);
@@ -99,9 +100,9 @@ struct Eng {
         if (!alive) return false;
         fence_proxy_async();           // this thread's global writes, for TMA reads after the barrier
         ++epoch;
-        const bool tr = cx.trace && blockIdx.x == 0 && tid == 0 && (int)epoch <= cx.trace_cap;
+        const bool tr = cx.trace && bid == 0 && tid == 0 && (int)epoch <= cx.trace_cap;
         if (tr) cx.trace[2 * (epoch - 1)] = (long long)globaltimer_ns();
-        alive = grid_sync(cx.bar, epoch, &cx.out->status, cx.timeout_ns, sflag);
+        alive = grid_sync(cx.bar, epoch, (unsigned)nblk, &cx.out->status, cx.timeout_ns, sflag);
         if (tr) cx.trace[2 * (epoch - 1) + 1] = (long long)globaltimer_ns();
         return alive;
     }
@@ -109,8 +110,8 @@ struct Eng {
     // record a failure status (first one wins); callers unwind uniformly
     __device__ void raise(int st) const { atomicCAS(&cx.out->status, ST_OK, st); }
 
-    __device__ long long gstride() const { return (long long)gridDim.x * blockDim.x; }
-    __device__ long long gstart() const { return (long long)blockIdx.x * blockDim.x + tid; }
+    __device__ long long gstride() const { return (long long)nblk * blockDim.x; }
+    __device__ long long gstart() const { return (long long)bid * blockDim.x + tid; }
 
     __device__ T *buf(int b) const { return cx.ws + (long long)b * cx.Np; }
     // offset of pixel (c, i, j) inside a buffer
@@ -255,16 +256,16 @@ struct Eng {
         else sync();
     }
 
-    __device__ S *partS(int slot) const { return reinterpret_cast<S *>(cx.part) + slot * gridDim.x; }
+    __device__ S *partS(int slot) const { return reinterpret_cast<S *>(cx.part) + slot * nblk; }
 
     // record this CTA's partial in a slot and return the grid total after a
     // barrier; every CTA obtains identical bits
     __device__ S reduce(S mine, int slot)
     {
         const S cta = block_sum<T>(mine, red);
-        if (tid == 0) partS(slot)[blockIdx.x] = cta;
+        if (tid == 0) partS(slot)[bid] = cta;
         if (!sync()) return Sc::zero();
-        return grid_total<T>(partS(slot), gridDim.x, gbuf, bcast);
+        return grid_total<T>(partS(slot), nblk, gbuf, bcast);
     }
 
     // acc += correlation of stage buffer s (kernel rows p0 .. p0+PC-1)
@@ -452,7 +453,7 @@ struct Eng {
             return gr * gr;
         });
         const S ss = reduce(part, 0);
-        if (alive && tid == 0 && blockIdx.x == 0) cx.out->gradnorm = sqrt(Sc::to_double(ss));
+        if (alive && tid == 0 && bid == 0) cx.out->gradnorm = sqrt(Sc::to_double(ss));
     }
 
     // B^T B v + alpha D^T(phi''(D x) . D v) for x, v in buffers bx, bv: to
@@ -532,12 +533,12 @@ struct Eng {
         int k = 0;
         for (;; ++k) {
             const int ycur = yc;
-            if (pending && warp == 0) grid_issue<T>(partS((k - 1) & 1), gridDim.x, gbuf);
+            if (pending && warp == 0) grid_issue<T>(partS((k - 1) & 1), nblk, gbuf);
             // phase A: U = B y_k - y
             residual(ycur, B_U);
             if (pending) {
                 if (warp == 0) {
-                    const S s = grid_finish<T>(gridDim.x, gbuf);
+                    const S s = grid_finish<T>(nblk, gbuf);
                     if (lane == 0) *bcast = s;
                 }
                 __syncthreads();
@@ -569,7 +570,7 @@ struct Eng {
                                     return gr * gr;
                                 });
             const S cta = block_sum<T>(part, red);
-            if (tid == 0) partS(k & 1)[blockIdx.x] = cta;
+            if (tid == 0) partS(k & 1)[bid] = cta;
             // momentum of the next iteration, before waiting on the barrier
             const S t_next = tn;
             const S tn_next = next_t(t_next);
@@ -577,7 +578,7 @@ struct Eng {
             if (!sync()) return k;
             passes += 2;
             if (k >= max_iters) {          // cap: the norm of y_k is needed now
-                const S ss = grid_total<T>(partS(k & 1), gridDim.x, gbuf, bcast);
+                const S ss = grid_total<T>(partS(k & 1), nblk, gbuf, bcast);
                 if (!Sc::finite(ss)) {
                     if (tid == 0) raise(ST_NONFINITE);
                     alive = false;
@@ -981,7 +982,7 @@ struct Eng {
         const int CKK = cx.C * cx.K * cx.K;
         long long passes = 0;
         int ll_iters = 0, cg_iters = 0, ll_capped = 0, cg_capped = 0, trials = 0, rounds = 0, accepted = 0;
-        int stopped = st.eps_stop > 0.0 && st.eps <= st.eps_stop;   // stop rule of Sec. 4.2
+        int stopped = (st.eps_stop > 0.0 && st.eps <= st.eps_stop) || st.halted;   // stop rule of Sec. 4.2
         double loss = 0.0, gxn = 0.0, znorm = 0.0, psi = 0.0, gn = 0.0, res = 0.0;
         if (!stopped) {
             import_dense(jb.x, B_XK);
@@ -1054,7 +1055,19 @@ struct Eng {
             if (accepted) export_dense(B_XK, (T *)jb.x);
             export_dense(B_Q, jb.q);
         }
-        if (tid == 0 && blockIdx.x == 0) {
+        if (tid == 0 && bid == 0) {
+            if (jb.maid_home) {        // device-resident state for the next launch (same bytes when unchanged)
+                MaidIn *h = jb.maid_home;
+                h->eps = st.eps; h->delta = st.delta; h->step = st.step; h->k = st.k;
+                if (rounds > 0 && !accepted && !stopped && alive) h->halted = 1;
+            }
+            if (cx.totals && rounds > 0) {
+                MaidTotals *t = cx.totals;
+                t->fused_iters += ll_iters + cg_iters;
+                t->conv_passes += passes;
+                t->upper_iters += 1;
+                t->accepted += accepted;
+            }
             DevOut *o = cx.out;
             o->accepted = accepted; o->rounds = rounds; o->trials = trials;
             o->ll_iters = ll_iters; o->cg_iters = cg_iters; o->ll_capped = ll_capped; o->cg_capped = cg_capped;
@@ -1065,20 +1078,12 @@ struct Eng {
     }
 };
 
+// The program of one call (selected by jb.mode) on one problem; every CTA of
+// the problem's grid or group runs it.
 template <typename T>
-__global__ void __launch_bounds__(MAXNW * 32, 1) adp_kernel(const __grid_constant__ Ctx<T> cx,
-                                                            const __grid_constant__ Job<T> jb)
+__device__ __forceinline__ void run_program(Eng<T> &e, const Ctx<T> &cx, const Job<T> &jb)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    using S = typename Scal<T>::S;
-    __shared__ S red[MAXNW];
-    __shared__ S bcast;
-    __shared__ double redd[MAXNW];
-    __shared__ T tau[MAXC];
-    __shared__ __align__(16) S gbuf[GT_MAX];
-    __shared__ int sflag;
-    Eng<T> e(cx, smem_raw, red, &bcast, redd, tau, gbuf, &sflag);
-    const bool lead = threadIdx.x == 0 && blockIdx.x == 0;
+    const bool lead = threadIdx.x == 0 && e.bid == 0;
     long long passes = 0;
     switch (jb.mode) {
     case M_IMPORT_Y: e.import_dense(jb.x, B_Y); break;
@@ -1158,12 +1163,53 @@ __global__ void __launch_bounds__(MAXNW * 32, 1) adp_kernel(const __grid_constan
     case M_WAIT_SELFTEST:
         // diagnostic: CTA 0 never arrives, so every other CTA's bounded wait at
         // this barrier runs out and records ST_TIMEOUT
-        if (blockIdx.x != 0) e.sync();
+        if (e.bid != 0) e.sync();
         break;
     default: break;
     }
     e.drain();
-    if (lead) cx.out->barriers = (int)e.epoch;
+    if (threadIdx.x == 0 && e.bid == 0) cx.out->barriers = (int)e.epoch;
+}
+
+#define ADP_KERNEL_SHARED                                        \
+    extern __shared__ __align__(128) unsigned char smem_raw[];   \
+    using S = typename Scal<T>::S;                               \
+    __shared__ S red[MAXNW];                                     \
+    __shared__ S bcast;                                          \
+    __shared__ double redd[MAXNW];                               \
+    __shared__ T tau[MAXC];                                      \
+    __shared__ __align__(16) S gbuf[GT_MAX];                     \
+    __shared__ int sflag
+
+// One problem per launch: the launch record lives in parameter space.
+template <typename T>
+__global__ void __launch_bounds__(MAXNW * 32, 1) adp_kernel(const __grid_constant__ Ctx<T> cx,
+                                                            const __grid_constant__ Job<T> jb)
+{
+    ADP_KERNEL_SHARED;
+    if (threadIdx.x == 0 && blockIdx.x == 0) cx.out->t_start = (long long)globaltimer_ns();
+    Eng<T> e(cx, gridDim.x, blockIdx.x, smem_raw, red, &bcast, redd, tau, gbuf, &sflag);
+    run_program<T>(e, cx, jb);
+    if (threadIdx.x == 0 && blockIdx.x == 0) cx.out->t_end = (long long)globaltimer_ns();
+}
+
+// Many problems per launch: CTAs first[g] .. first[g+1]-1 form problem g's
+// group (its own barrier counter, reductions and result record); the launch
+// records live in global memory (tensor maps included, 64-byte aligned).
+template <typename T>
+__global__ void __launch_bounds__(MAXNW * 32, 1) adp_kernel_batched(const Ctx<T> *__restrict__ ctxs,
+                                                                    const Job<T> *__restrict__ jobs,
+                                                                    const int *__restrict__ first, int n)
+{
+    ADP_KERNEL_SHARED;
+    int g = 0;
+    while (g + 1 < n && (int)blockIdx.x >= __ldg(first + g + 1)) ++g;
+    const int f0 = __ldg(first + g), nb = __ldg(first + g + 1) - f0;
+    const Ctx<T> &cx = ctxs[g];
+    if (threadIdx.x == 0 && blockIdx.x == (unsigned)f0) cx.out->t_start = (long long)globaltimer_ns();
+    Eng<T> e(cx, nb, (int)blockIdx.x - f0, smem_raw, red, &bcast, redd, tau, gbuf, &sflag);
+    run_program<T>(e, cx, jobs[g]);
+    if (threadIdx.x == 0 && blockIdx.x == (unsigned)f0) cx.out->t_end = (long long)globaltimer_ns();
 }
 
 } // namespace adp
