@@ -9,13 +9,16 @@ One step = one complete MAID run (Algorithm 2) from b_0 and x_0 = y until the
 stop rule of Sec. 4.2 fires (eps <= eps_stop) or MAX_UPPER upper iterations
 have run: the lower-level FISTA solves, the upper losses, the CG solves of the
 IFT hypergradient, the kernel-gradient correlations and the backtracking
-trials.  Each upper iteration is one cooperative launch of libadp
-(adp_maid_step); the host only reads the scalars at its end.
+trials.  Each upper iteration is one cooperative launch of libadp, and a run
+is a CUDA graph of MAX_UPPER such launches replayed with the MAID state kept
+on the device (adp_batch_maid_run_graph, a batch of one problem); launches
+after the stop rule return at once.
 
 value: Mvalue*iter/s = (C*H*W values) x (FISTA + CG iterations executed in
 the timed runs) / device time of those runs, summed over ranks (replicas).
-Beside it: the time to tolerance per run, and the same runs driven from the
-host with one launch per solve ("plain GPU MAID").
+Beside it: the time to tolerance per run, the same runs stepped from the host
+(one launch per upper iteration, adp_maid_step), and driven from the host with
+one launch per solve ("plain GPU MAID").
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -170,6 +173,21 @@ def maid_run(prob, a, y, b_h=None, x_h=None):
     return ms, iters, passes, ups, acc, b, x, st
 
 
+def maid_run_graph(batch, prob, bufs, b0, x0):
+    """One MAID run as a device-resident CUDA graph of MAX_UPPER steps (a
+    batch of one problem; state kept on the device, steps after the stop rule
+    return at once) on the persistent buffers bufs = (b, x, q), started from
+    b0, x0.  Returns (graph device ms, fused iters, conv passes, upper
+    iterations, accepted, b, x, state)."""
+    b, x, q = bufs
+    b.copy_(b0)
+    x.copy_(x0)
+    q.zero_()
+    st = prob.maid_init(eps=EPS0, delta=EPS0, step=STEP0, eps_stop=EPS_STOP)
+    (fused, passes, ups, acc), = batch.maid_run_graph([st], [b], [x], [q], MAX_UPPER)
+    return batch.last_kernel_ms(), fused, passes, ups, acc, b, x, st
+
+
 def plain_maid_run(prob, a, y):
     """The same Algorithm 2 driven from the host: one launch per lower-level
     solve, upper loss and hypergradient, scalars read back after each (the
@@ -253,8 +271,10 @@ def run_ours(args):
     y = torch.tensor(inst.y, dtype=torch.float32, device=dev)
     a = torch.tensor(inst.a, dtype=torch.float32, device=dev)
     prob = adp.Problem(adp.Params(C, H, W, K, alpha=1e-2, reg_param=1e-2, beta=0.3), y, a)
+    batch = adp.Batch([prob])
+    bufs = (torch.empty_like(a), torch.empty_like(y), torch.empty_like(y))
     for _ in range(args.warmup):
-        maid_run(prob, a, y)
+        maid_run_graph(batch, prob, bufs, a, y)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -268,7 +288,7 @@ def run_ours(args):
     for _ in range(args.steps):
         flush.zero_()                       # L2 flush between timed runs (not timed)
         ev0.record()
-        kms, it, ps, u, acc, b, x, st = maid_run(prob, a, y)
+        kms, it, ps, u, acc, b, x, st = maid_run_graph(batch, prob, bufs, a, y)
         ev1.record()
         ev1.synchronize()
         run_ms.append(ev0.elapsed_time(ev1))
@@ -287,9 +307,19 @@ def run_ours(args):
     tot_ms_max, units_all = reduce_over_ranks(tot_ms, units, dev)
     value = units_all / (tot_ms_max / 1e3) / 1e6
 
-    xr, br = x.double().cpu().numpy(), b.double().cpu().numpy()
+    xr, br = x.double().cpu().numpy(), b.double().cpu().numpy()   # the last timed run's result
     psnr_x = 10 * np.log10(1.0 / np.mean((xr - inst.x_true) ** 2))
     psnr_b = 10 * np.log10(float(np.max(inst.b_true)) ** 2 / np.mean((br - inst.b_true) ** 2))
+
+    # the same runs stepped from the host (one launch per upper iteration)
+    maid_run(prob, a, y)
+    hs_ms = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        maid_run(prob, a, y)
+        torch.cuda.synchronize()
+        hs_ms.append((time.perf_counter() - t0) * 1e3)
 
     # the plain host-driven GPU MAID on the same runs (two runs, the first warm)
     plain_maid_run(prob, a, y)
@@ -309,7 +339,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         bd.copy_(b0_h, non_blocking=True)
         xd.copy_(x0_h, non_blocking=True)
-        _, it, _, _, _, b2, x2, st2 = maid_run(prob, a, y, bd, xd)
+        _, it, _, _, _, b2, x2, st2 = maid_run_graph(batch, prob, bufs, bd, xd)
         bo_h.copy_(b2, non_blocking=True)
         xo_h.copy_(x2, non_blocking=True)
         torch.cuda.synchronize()
@@ -335,19 +365,22 @@ def run_ours(args):
                    "max_upper": MAX_UPPER, "step": "one MAID run to the stop rule",
                    "l2": "flushed between timed runs (256 MB write)", "parallelism": f"replicas x{world}"},
         "maid": {"time_to_tolerance_s": tot_ms_max / args.steps / 1e3,
+                 "form": "device-resident run: one CUDA graph of up to max_upper cooperative launches",
+                 "host_stepped_s": statistics.median(hs_ms) / 1e3,
                  "plain_gpu_maid_s": pms / 1e3, "speedup_vs_plain": pms / (tot_ms_max / args.steps),
                  "upper_iters_per_run": ups / args.steps, "accepted_per_run": accepted / args.steps,
                  "fused_iters_per_run": iters / args.steps, "eps_end": st.eps, "stopped": bool(st.stopped),
                  "final_psnr_x_db": psnr_x, "final_psnr_b_db": psnr_b, "plain_final_psnr_x_db": plain_psnr,
-                 "grid_ctas": prob.grid_size(), "warps_per_cta": prob.warps_per_cta()},
+                 "grid_ctas": prob.grid_size(), "warps_per_cta": prob.warps_per_cta(),
+                 "graph_device_ms_per_run": kern_ms / args.steps},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved / peak_tf, "traffic": traffic,
-                     "kernel": "adp_kernel<float> (persistent MAID step)",
+                     "kernel": "adp_kernel<float> (persistent MAID step, graph-replayed)",
                      "peak_basis": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
                      "flops_basis": "2 K^2 C H W per convolution pass, passes counted on the device"},
         "e2e": {"value": e2e_units / (e2e_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": ups,
+        "gpu_launches": args.steps * MAX_UPPER,
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

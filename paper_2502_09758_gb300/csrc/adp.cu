@@ -166,6 +166,7 @@ static adp_status launch(adp_problem *p, Job<T> &jb)
     const int st = p->hout->status;
     if (st == ST_TIMEOUT) return set_err(ADP_ETIMEOUT, "device-side wait gave up after %s%lld ns", "", cx.timeout_ns);
     if (st == ST_NONFINITE) return set_err(ADP_ENONFINITE, "non-finite value in a reduction%s", "", 0);
+    if (st == ST_ALIGN) return set_err(ADP_ECUDA, "dynamic shared memory not 128-byte aligned%s", "", 0);
     if (st != ST_OK) return set_err(ADP_ECUDA, "unexpected device status%s %lld", "", st);
     return ADP_OK;
 }
@@ -245,6 +246,10 @@ adp_status adp_problem_create(const adp_params *prm, const void *y, const void *
     p->esize = q.prec == ADP_F32 ? sizeof(float) : sizeof(double);
     p->g = q.prec == ADP_F32 ? make_geom<float>(q.C, q.H, q.W, q.K) : make_geom<double>(q.C, q.H, q.W, q.K);
     const Geom &g = p->g;
+    if (g.Np >= (1LL << 31)) {     // pixel offsets inside a padded image are 32-bit
+        adp_problem_destroy(p);
+        return set_err(ADP_EINVAL, "padded image too large%s (%lld elements, limit 2^31)", "", g.Np);
+    }
     const int MR = q.prec == ADP_F32 ? Cfg<float>::MR : Cfg<double>::MR;
     const int NX = q.prec == ADP_F32 ? Cfg<float>::PC + MR - 1 : Cfg<double>::PC + MR - 1;
 
@@ -267,16 +272,16 @@ adp_status adp_problem_create(const adp_params *prm, const void *y, const void *
     // warps per CTA: as many as shared memory allows (the kernel's static shared
     // memory is below 5 KB; keep that margin)
     int nw = MAXNW, total = 0;
-    for (; nw >= 1; --nw) {
+    for (; nw >= 2; nw -= 2) {   // warps work in pairs
         total = q.prec == ADP_F32 ? Layout<float>(q.C, q.K, nw, g.wsm).total : Layout<double>(q.C, q.K, nw, g.wsm).total;
-        if ((size_t)total * p->esize + 128 + 5 * 1024 <= (size_t)maxsmem) break;
+        if ((size_t)total * p->esize + 5 * 1024 <= (size_t)maxsmem) break;
     }
-    if (nw < 1) {
+    if (nw < 2) {
         adp_problem_destroy(p);
         return set_err(ADP_EINVAL, "kernel too large for shared memory%s (K = %lld)", "", q.K);
     }
     p->nw = nw;
-    p->smem = (size_t)total * p->esize + 128;   // + alignment slack of the TMA destinations
+    p->smem = (size_t)total * p->esize;
     const void *kfn = q.prec == ADP_F32 ? kernel_f32() : kernel_f64();
     // opt in to the device's whole dynamic shared memory (less the static part)
     // rather than this problem's size: the attribute is shared by every problem
@@ -520,6 +525,10 @@ struct adp_batch {
     unsigned char *hctx, *hjob;   // pinned staging of the launch records
     cudaEvent_t ev0, ev1;
     float last_ms;
+    cudaStream_t cs;              // capture / replay stream of device-resident runs
+    cudaGraphExec_t gexec;        // instantiated graph of the last run shape
+    int gsteps, ggrid;            // its steps and CTAs
+    std::vector<unsigned char> gctx;   // batch of one: the records the graph captured by value
 };
 
 static const size_t kBarStride = 64;   // unsigned counters, 256 bytes apart
@@ -534,6 +543,8 @@ static void batch_free(adp_batch *bt)
     if (bt->hjob) cudaFreeHost(bt->hjob);
     if (bt->ev0) cudaEventDestroy(bt->ev0);
     if (bt->ev1) cudaEventDestroy(bt->ev1);
+    if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
+    if (bt->cs) cudaStreamDestroy(bt->cs);
     delete bt;
 }
 
@@ -617,6 +628,8 @@ static adp_status batch_report(adp_batch *bt, adp_maid_state *st, const MaidIn *
         adp_maid_state *s = st + i;
         if (o->status == ST_TIMEOUT && first_bad == ADP_OK) first_bad = set_err(ADP_ETIMEOUT, "device-side wait gave up%s", "", 0);
         if (o->status == ST_NONFINITE && first_bad == ADP_OK) first_bad = set_err(ADP_ENONFINITE, "non-finite value in a reduction%s", "", 0);
+        if (o->status != ST_OK && first_bad == ADP_OK)
+            first_bad = set_err(ADP_ECUDA, "unexpected device status for problem %s%lld", "", i);
         if (o->status != ST_OK) continue;
         if (resident_state) {
             const MaidIn &m = resident_state[i];
@@ -634,13 +647,20 @@ static adp_status batch_report(adp_batch *bt, adp_maid_state *st, const MaidIn *
     return first_bad;
 }
 
+// One batched launch.  A batch of one problem launches the single-problem
+// kernel with its records by value (parameter space, as adp_maid_step does);
+// a device-resident run then finds its MAID state through the job's maid_home.
 static adp_status batch_launch(adp_batch *bt, cudaStream_t stream)
 {
-    const void *fn = bt->prec == ADP_F32 ? kernel_f32_batched() : kernel_f64_batched();
+    const bool one = bt->n == 1;
+    const void *fn = one ? (bt->prec == ADP_F32 ? kernel_f32() : kernel_f64())
+                         : (bt->prec == ADP_F32 ? kernel_f32_batched() : kernel_f64_batched());
     void *ctxp = bt->dctx, *jobp = bt->djob;
     int *fp = bt->dfirst;
     int n = bt->n;
-    void *args[] = {&ctxp, &jobp, &fp, &n};
+    void *args_many[] = {&ctxp, &jobp, &fp, &n};
+    void *args_one[] = {bt->hctx, bt->hjob};
+    void **args = one ? args_one : args_many;
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof cfg);
     cfg.gridDim = dim3((unsigned)bt->first[n]);
@@ -686,7 +706,7 @@ adp_status adp_batch_create(adp_problem *const *ps, int n, adp_batch **out)
         const Geom &g = p->g;
         const int tot = bt->prec == ADP_F32 ? Layout<float>(p->prm.C, p->prm.K, nw, g.wsm).total
                                             : Layout<double>(p->prm.C, p->prm.K, nw, g.wsm).total;
-        smem = std::max(smem, (size_t)tot * bt->esize + 128);
+        smem = std::max(smem, (size_t)tot * bt->esize);
     }
     bt->smem = smem;
     adp_status st = ADP_OK;
@@ -716,6 +736,11 @@ adp_status adp_batch_create(adp_problem *const *ps, int n, adp_batch **out)
     long long cap = 0;
     for (adp_problem *p : bt->ps) cap += p->grid;
     if (cap < bt->max_ctas) bt->max_ctas = (int)cap;
+    if (n == 1) {                  // the single-problem kernel with the problem's own launch shape
+        bt->nw = ps[0]->nw;
+        bt->smem = ps[0]->smem;
+        bt->max_ctas = ps[0]->grid;
+    }
     bt->work.resize(n);
     for (int i = 0; i < n; ++i) bt->work[i] = (double)ps[i]->g.nstrips * ps[i]->prm.K * ps[i]->prm.K;
     batch_partition(bt);
@@ -813,35 +838,52 @@ adp_status adp_batch_maid_run_graph(adp_batch *bt, adp_maid_state *st, void *con
     CK(cudaMemcpyAsync(bt->dfirst, bt->first.data(), (bt->n + 1) * sizeof(int), cudaMemcpyHostToDevice, stream));
     CK(cudaMemsetAsync(bt->dtot, 0, bt->n * sizeof(MaidTotals), stream));
     CK(cudaStreamSynchronize(stream));
-    // capture the steps on a private stream (the legacy default stream cannot be captured)
-    cudaStream_t cs;
-    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    // the steps are captured once per run shape (steps, CTAs) on a private
+    // stream (the legacy default stream cannot be captured) and replayed; the
+    // launch records they read are uploaded above, before every replay
     adp_status res = ADP_OK;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        for (int s = 0; s < max_steps && res == ADP_OK; ++s) res = batch_launch(bt, cs);
-        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
-        if (res == ADP_OK && e2 != cudaSuccess) res = set_err(ADP_ECUDA, "graph capture: %s%lld", cudaGetErrorString(e2), 0);
-    } else {
-        res = set_err(ADP_ECUDA, "graph capture: %s%lld", cudaGetErrorString(e), 0);
+    if (!bt->cs) CK(cudaStreamCreateWithFlags(&bt->cs, cudaStreamNonBlocking));
+    // (a resident run reads its MAID state through maid_home, so the job's own
+    // copy of the state, its last field, does not enter the comparison)
+    const size_t jcmp = bt->prec == ADP_F32 ? offsetof(Job<float>, maid) : offsetof(Job<double>, maid);
+    const bool same_records = bt->n > 1 || (bt->gctx.size() == bt->ctx_bytes + bt->job_bytes &&
+                                            !memcmp(bt->gctx.data(), bt->hctx, bt->ctx_bytes) &&
+                                            !memcmp(bt->gctx.data() + bt->ctx_bytes, bt->hjob, jcmp));
+    if (!bt->gexec || bt->gsteps != max_steps || bt->ggrid != bt->first[bt->n] || !same_records) {
+        if (bt->n == 1) {          // records captured by value: remember them
+            bt->gctx.assign(bt->hctx, bt->hctx + bt->ctx_bytes);
+            bt->gctx.insert(bt->gctx.end(), bt->hjob, bt->hjob + bt->job_bytes);
+        }
+        if (bt->gexec) { cudaGraphExecDestroy(bt->gexec); bt->gexec = nullptr; }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(bt->cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int s = 0; s < max_steps && res == ADP_OK; ++s) res = batch_launch(bt, bt->cs);
+            cudaError_t e2 = cudaStreamEndCapture(bt->cs, &graph);
+            if (res == ADP_OK && e2 != cudaSuccess)
+                res = set_err(ADP_ECUDA, "graph capture: %s%lld", cudaGetErrorString(e2), 0);
+        } else {
+            res = set_err(ADP_ECUDA, "graph capture: %s%lld", cudaGetErrorString(e), 0);
+        }
+        if (res == ADP_OK) {
+            e = cudaGraphInstantiate(&bt->gexec, graph, 0);
+            if (e != cudaSuccess) {
+                bt->gexec = nullptr;
+                res = set_err(ADP_ECUDA, "graph instantiation: %s%lld", cudaGetErrorString(e), 0);
+            }
+        }
+        if (graph) cudaGraphDestroy(graph);
+        bt->gsteps = max_steps;
+        bt->ggrid = bt->first[bt->n];
     }
     if (res == ADP_OK) {
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        if (e != cudaSuccess) res = set_err(ADP_ECUDA, "graph instantiation: %s%lld", cudaGetErrorString(e), 0);
-    }
-    if (res == ADP_OK) {
-        cudaEventRecord(bt->ev0, cs);
-        e = cudaGraphLaunch(exec, cs);
-        cudaEventRecord(bt->ev1, cs);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+        cudaEventRecord(bt->ev0, bt->cs);
+        cudaError_t e = cudaGraphLaunch(bt->gexec, bt->cs);
+        cudaEventRecord(bt->ev1, bt->cs);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(bt->cs);
         if (e != cudaSuccess) res = set_err(ADP_ECUDA, "graph launch: %s%lld", cudaGetErrorString(e), 0);
         else cudaEventElapsedTime(&bt->last_ms, bt->ev0, bt->ev1);
     }
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    cudaStreamDestroy(cs);
     if (res != ADP_OK) return res;
     CK(cudaMemcpy(bt->hout, bt->dout, bt->n * sizeof(DevOut), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(bt->hjob, bt->djob, bt->n * bt->job_bytes, cudaMemcpyDeviceToHost));

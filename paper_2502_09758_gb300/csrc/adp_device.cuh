@@ -23,7 +23,7 @@ template <> struct Cfg<float>  { static constexpr int MR = 8, PC = 16; };
 template <> struct Cfg<double> { static constexpr int MR = 4, PC = 8; };
 
 // Status words shared with the host (values equal adp_status).
-enum : int { ST_OK = 0, ST_NONFINITE = 4, ST_NOCONV = 5, ST_LSFAIL = 6, ST_TIMEOUT = 7 };
+enum : int { ST_OK = 0, ST_NONFINITE = 4, ST_NOCONV = 5, ST_LSFAIL = 6, ST_TIMEOUT = 7, ST_ALIGN = 100 };
 
 // Written by the device, copied to pinned host memory after each launch.
 struct DevOut {
@@ -363,6 +363,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, unsigned parity, long 
     }
 }
 
+// plain arrival (count 1) on an mbarrier, release semantics at CTA scope
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int w,
                                             uint64_t *mbar)
 {
@@ -380,16 +386,16 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Register-blocked direct correlation of one 32-column x MR-row strip over
-// one stage: PC consecutive kernel rows p0 .. p0+PC-1, all K kernel columns.
-//   acc[m] += sum_{q<K} sum_{p<PC} w[q*Kp + p] * s[(m + p)*pitch + lj + q]
+// one stage: PC consecutive kernel rows p0 .. p0+PC-1, kernel columns q0 .. K-1.
+//   acc[m] += sum_{q0<=q<K} sum_{p<PC} w[q*Kp + p] * s[(m + p)*pitch + lj + q]
 // s holds the PC + MR - 1 tile rows of the stage; w points at row p0 of a
 // kernel stored column-major (w[q][p], p contiguous, rows zero-padded to Kp).
 // Per kernel column the thread needs PC + MR - 1 values of its tile column and
 // PC weights (vector loads, the same address in every lane); they are loaded
 // one column ahead of the MR x PC FMAs that use them, so load latency
-// overlaps arithmetic.  The weights come through a generic pointer: shared
-// memory, or global memory read through L1 (coherent after the grid barrier
-// that follows their writing).
+// overlaps arithmetic.  The weights are in shared memory, or in global memory
+// read through L1 (coherent after the grid barrier that follows their
+// writing); the caller's pointer provenance decides which loads are emitted.
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using V = float4; static constexpr int L = 4; };
 template <> struct Vec4<double> { using V = double2; static constexpr int L = 2; };
@@ -409,7 +415,7 @@ __device__ __forceinline__ void load_wchunk(const T *wq, T (&wv)[PC])
 }
 
 template <typename T, int MR, int PC>
-__device__ __forceinline__ void corr_stage(const T *__restrict__ s, int pitch, const T *w, int K,
+__device__ __forceinline__ void corr_stage(const T *__restrict__ s, int pitch, const T *w, int q0, int K,
                                            int Kp, int lj, T (&acc)[MR])
 {
     constexpr int NX = PC + MR - 1;
@@ -428,8 +434,10 @@ __device__ __forceinline__ void corr_stage(const T *__restrict__ s, int pitch, c
 #pragma unroll
             for (int m = 0; m < MR; ++m) acc[m] = fma(wv[p], xv[m + p], acc[m]);
     };
+    q = q0;
+    if (q0 >= K) return;
     load(xa, wa);
-    int qi = 0;
+    int qi = q0;
     for (; qi + 2 <= K; qi += 2) {
         load(xb, wb);
         comp(xa, wa);
@@ -514,7 +522,7 @@ struct Ctx {
     int BW;                            // stage box width: columns col0 - r4 .. col0 - r4 + BW - 1
     int nx, ny, nstrips;               // strips: nx per row band, ny bands per channel
     int wsm;                           // 1: kernel weights in shared memory, 0: in wg (read through L1)
-    int multiwrap;                     // 1 when Gx > W or Gy > H (ghosts hold several periods)
+    int multiwrap;                     // 1 when 2Gx > W or 2Gy > H (a pixel may have several copies per axis)
     long long N, HW, HWp, Np;          // dense and padded sizes (Np = C*Hp*Wp per buffer)
     long long *trace;                  // optional: barrier timestamps of CTA 0 (arrive, leave)
     int trace_cap;
@@ -570,7 +578,7 @@ struct Layout {
         tile1 = round_up((MR + 2) * 40, 32);
         tileI = round_up(MR * 32, 32);
         w_elems = wsm ? round_up(2 * C * Kp * K, 32) : 0;
-        warp_elems = 2 * stage + 2 * tile1 + tileI + 32;
+        warp_elems = 2 * stage + 2 * tile1 + tileI + 32;   // 32: the mbarriers
         total = w_elems + nw * warp_elems;
     }
 };
@@ -602,7 +610,7 @@ inline Geom make_geom(int C, int H, int W, int K)
     g.ny = (H + MR - 1) / MR;
     g.nstrips = C * g.nx * g.ny;
     g.wsm = (long long)2 * C * K * g.Kp * (long long)sizeof(T) <= WSMEM_MAX_BYTES ? 1 : 0;
-    g.multiwrap = (g.Gx > W || g.Gy > H) ? 1 : 0;
+    g.multiwrap = (2 * g.Gx > W || 2 * g.Gy > H) ? 1 : 0;
     g.HW = (long long)H * W;
     g.HWp = (long long)g.Hp * g.Wp;
     g.N = g.HW * C;

@@ -107,12 +107,12 @@ adp_status run_noalloc(const adp_params &q, DeviceSetup &ds, const void *y, cons
     if ((size_t)4 * q.C * q.K * g.Kp * sizeof(T) > kWeightBytes)
         return fail(ADP_EINVAL, "kernel weights exceed the no-allocation limit (4*C*K*Kp*element size)");
     int total = 0, nw = MAXNW;
-    for (; nw >= 1; --nw) {
+    for (; nw >= 2; nw -= 2) {   // warps work in pairs
         total = Layout<T>(q.C, q.K, nw, g.wsm).total;
-        if ((size_t)total * sizeof(T) + 128 + 5 * 1024 <= (size_t)ds.maxsmem) break;
+        if ((size_t)total * sizeof(T) + 5 * 1024 <= (size_t)ds.maxsmem) break;
     }
-    if (nw < 1) return fail(ADP_EINVAL, "kernel size too large for shared memory");
-    const size_t smem = (size_t)total * sizeof(T) + 128;   // + alignment slack of the TMA destinations
+    if (nw < 2) return fail(ADP_EINVAL, "kernel size too large for shared memory");
+    const size_t smem = (size_t)total * sizeof(T);
     const void *fn = sizeof(T) == 4 ? kernel_f32() : kernel_f64();
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * nw, smem) != cudaSuccess || occ < 1)
