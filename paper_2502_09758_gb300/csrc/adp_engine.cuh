@@ -45,6 +45,14 @@ __shared__ __align__(16) double g_tau[MAXC];
 __shared__ __align__(16) double g_gbuf[GT_MAX];
 __shared__ int g_sflag;
 
+// Report of a MAID step, accumulated by thread 0 of each CTA (shared memory,
+// so that it occupies no registers while the solves run).
+struct MaidRep {
+    int ll_iters, cg_iters, ll_capped, cg_capped, trials;
+    double loss, gxn, znorm, psi;
+};
+__shared__ MaidRep g_rep;
+
 template <typename T>
 struct Eng {
     using Sc = Scal<T>;
@@ -985,105 +993,114 @@ struct Eng {
     // ------------------------------------------------------------ MAID
     // One upper iteration of Algorithm 2; every CTA runs the same control flow
     // on identical reduction results.  x~(b_k) is imported into B_XK; the trial
-    // solutions go to B_XT.
+    // solutions go to B_XT.  Register economy: the run's constant parameters
+    // are read from the job (or its device-resident home) where used, the
+    // report is accumulated in shared memory by thread 0, and only the
+    // adaptive quantities and the current comparison terms stay in registers.
     __device__ void maid(const Job<T> &jb)
     {
-        MaidIn st = jb.maid_home ? *jb.maid_home : jb.maid;   // device-resident runs carry the state over
+        const MaidIn &M = jb.maid_home ? *jb.maid_home : jb.maid;   // constant fields
+        MaidRep &R = g_rep;
+        double eps = M.eps, delta = M.delta, step = M.step;
+        int k = M.k;
         T *b = jb.bio;
         const int CKK = cx.C * cx.K * cx.K;
         long long passes = 0;
-        int ll_iters = 0, cg_iters = 0, ll_capped = 0, cg_capped = 0, trials = 0, rounds = 0, accepted = 0;
-        int stopped = (st.eps_stop > 0.0 && st.eps <= st.eps_stop) || st.halted;   // stop rule of Sec. 4.2
-        double loss = 0.0, gxn = 0.0, znorm = 0.0, psi = 0.0, gn = 0.0, res = 0.0;
+        bool stopped = (M.eps_stop > 0.0 && eps <= M.eps_stop) || M.halted;   // stop rule of Sec. 4.2
+        bool accepted = false;
+        int rounds = 0;
+        if (tid() == 0) R = MaidRep{};
+        __syncthreads();
         if (!stopped) {
             import_dense(jb.x, B_XK);
-            if (!sync()) stopped = 1;
+            if (!sync()) stopped = true;
         }
-        int j = st.max_bt;
-        for (int round = 0; round < st.max_rounds && alive && !stopped; ++round, ++j) {
+        int j = M.max_bt;
+        for (int round = 0; round < M.max_rounds && alive && !stopped; ++round, ++j) {
             rounds = round + 1;
             // InexactGradient(b_k, eps_k, delta_k)
-            ll_iters += lower_solve(b, B_XK, B_XK, st.eps, st.ll_max_iters, gn, passes);
+            double gn = 0.0, res = 0.0;
+            int it = lower_solve(b, B_XK, B_XK, eps, M.ll_max_iters, gn, passes);
+            if (tid() == 0) { R.ll_iters += it; if (gn > eps) R.ll_capped = 1; }
             if (!sync()) break;
-            if (gn > st.eps) ll_capped = 1;
             double l0 = 0.0, gx0 = 0.0;
             upper_loss(b, B_XK, l0, gx0, passes);
             if (!alive) break;
             int capped = 0;
-            cg_iters += cg(b, B_XK, B_G, st.delta, st.cg_max_iters, true, res, capped, passes);
+            it = cg(b, B_XK, B_G, delta, M.cg_max_iters, true, res, capped, passes);
+            if (tid() == 0) { R.cg_iters += it; if (capped) R.cg_capped = 1; }
             if (!alive) break;
-            if (capped) cg_capped = 1;
             if (!sync()) break;
             const double zz = cross(b, B_XK, B_Q, cx.ZK, true, true, passes);
             if (!alive) break;
-            znorm = sqrt(zz);
-            if (!isfinite(znorm)) {
+            if (tid() == 0) R.znorm = sqrt(zz);
+            if (!isfinite(zz)) {
                 if (tid() == 0) raise(ST_NONFINITE);
                 alive = false;
                 break;
             }
             bool done = false;
             for (int i = 0; i < j; ++i) {
-                ++trials;
+                if (tid() == 0) ++R.trials;
                 // b' = b - step z
                 for (long long e = gstart(); e < CKK; e += gstride())
-                    cx.BT[e] = (T)((double)__ldcg(b + e) - st.step * (double)__ldcg(cx.ZK + e));
+                    cx.BT[e] = (T)((double)__ldcg(b + e) - step * (double)__ldcg(cx.ZK + e));
                 if (!sync()) break;
                 double g1 = 0.0;
-                ll_iters += lower_solve(cx.BT, B_XK, B_XT, st.eps, st.ll_max_iters, g1, passes);
+                it = lower_solve(cx.BT, B_XK, B_XT, eps, M.ll_max_iters, g1, passes);
+                if (tid() == 0) { R.ll_iters += it; if (g1 > eps) R.ll_capped = 1; }
                 if (!sync()) break;
-                if (g1 > st.eps) ll_capped = 1;
                 double l1 = 0.0, gx1 = 0.0;
                 upper_loss(cx.BT, B_XT, l1, gx1, passes);
                 if (!alive) break;
                 // psi of Eq. 3.4 with eps_bar = eps_k
-                const double eb = st.eps;
-                psi = l1 + gx1 * eb + 0.5 * st.L_gx * eb * eb - l0 + gx0 * eb + st.lambda * st.step * zz;
+                const double eb = eps;
+                const double psi = l1 + gx1 * eb + 0.5 * M.L_gx * eb * eb - l0 + gx0 * eb + M.lambda * step * zz;
+                if (tid() == 0) R.psi = psi;
                 if (psi <= 0.0) {
                     for (long long e = gstart(); e < CKK; e += gstride()) b[e] = __ldcg(cx.BT + e);
                     copy_buf(B_XK, -1, B_XT);
-                    loss = l1;
-                    gxn = gx1;
-                    st.eps *= st.nu_up;
-                    st.delta *= st.nu_up;
-                    st.step *= st.rho_up;
-                    st.k += 1;
-                    accepted = 1;
+                    if (tid() == 0) { R.loss = l1; R.gxn = gx1; }
+                    eps *= M.nu_up;
+                    delta *= M.nu_up;
+                    step *= M.rho_up;
+                    k += 1;
+                    accepted = true;
                     done = true;
                     break;
                 }
-                st.step *= st.rho_down;
+                step *= M.rho_down;
             }
             if (done || !alive) break;
-            loss = l0;
-            gxn = gx0;
-            st.eps *= st.nu_down;
-            st.delta *= st.nu_down;
-            if (st.eps_stop > 0.0 && st.eps <= st.eps_stop) stopped = 1;
+            if (tid() == 0) { R.loss = l0; R.gxn = gx0; }
+            eps *= M.nu_down;
+            delta *= M.nu_down;
+            if (M.eps_stop > 0.0 && eps <= M.eps_stop) stopped = true;
         }
         // x~ and q back to the caller (x unchanged unless a step was accepted)
         if (alive && rounds > 0 && sync()) {
             if (accepted) export_dense(B_XK, (T *)jb.x);
             export_dense(B_Q, jb.q);
         }
+        __syncthreads();               // thread 0's report entries are complete
         if (tid() == 0 && bid == 0) {
             if (jb.maid_home) {        // device-resident state for the next launch (same bytes when unchanged)
                 MaidIn *h = jb.maid_home;
-                h->eps = st.eps; h->delta = st.delta; h->step = st.step; h->k = st.k;
+                h->eps = eps; h->delta = delta; h->step = step; h->k = k;
                 if (rounds > 0 && !accepted && !stopped && alive) h->halted = 1;
             }
             if (cx.totals && rounds > 0) {
                 MaidTotals *t = cx.totals;
-                t->fused_iters += ll_iters + cg_iters;
+                t->fused_iters += R.ll_iters + R.cg_iters;
                 t->conv_passes += passes;
                 t->upper_iters += 1;
-                t->accepted += accepted;
+                t->accepted += accepted ? 1 : 0;
             }
             DevOut *o = cx.out;
-            o->accepted = accepted; o->rounds = rounds; o->trials = trials;
-            o->ll_iters = ll_iters; o->cg_iters = cg_iters; o->ll_capped = ll_capped; o->cg_capped = cg_capped;
-            o->k = st.k; o->eps = st.eps; o->delta = st.delta; o->step = st.step;
-            o->loss = loss; o->gradx_norm = gxn; o->znorm = znorm; o->psi = psi;
+            o->accepted = accepted; o->rounds = rounds; o->trials = R.trials;
+            o->ll_iters = R.ll_iters; o->cg_iters = R.cg_iters; o->ll_capped = R.ll_capped; o->cg_capped = R.cg_capped;
+            o->k = k; o->eps = eps; o->delta = delta; o->step = step;
+            o->loss = R.loss; o->gradx_norm = R.gxn; o->znorm = R.znorm; o->psi = R.psi;
             o->conv_passes = passes; o->stopped = stopped;
         }
     }
