@@ -9,10 +9,10 @@ One step = one complete MAID run (Algorithm 2) from b_0 and x_0 = y until the
 stop rule of Sec. 4.2 fires (eps <= eps_stop) or MAX_UPPER upper iterations
 have run: the lower-level FISTA solves, the upper losses, the CG solves of the
 IFT hypergradient, the kernel-gradient correlations and the backtracking
-trials.  Each upper iteration is one cooperative launch of libadp, and a run
-is a CUDA graph of MAX_UPPER such launches replayed with the MAID state kept
-on the device (adp_batch_maid_run_graph, a batch of one problem); launches
-after the stop rule return at once.
+trials.  A whole run is one cooperative launch of libadp that loops over
+the upper iterations on the device until the stop rule
+(adp_batch_maid_run_graph on a batch of one problem; the launch is replayed
+from a CUDA graph).
 
 value: Mvalue*iter/s = (C*H*W values) x (FISTA + CG iterations executed in
 the timed runs) / device time of those runs, summed over ranks (replicas).
@@ -174,11 +174,11 @@ def maid_run(prob, a, y, b_h=None, x_h=None):
 
 
 def maid_run_graph(batch, prob, bufs, b0, x0):
-    """One MAID run as a device-resident CUDA graph of MAX_UPPER steps (a
-    batch of one problem; state kept on the device, steps after the stop rule
-    return at once) on the persistent buffers bufs = (b, x, q), started from
-    b0, x0.  Returns (graph device ms, fused iters, conv passes, upper
-    iterations, accepted, b, x, state)."""
+    """One MAID run in one cooperative launch (a batch of one problem, the
+    launch replayed from a CUDA graph; up to MAX_UPPER upper iterations, ended
+    by the stop rule) on the persistent buffers bufs = (b, x, q), started from
+    b0, x0.  Returns (device ms, fused iters, conv passes, upper iterations,
+    accepted, b, x, state)."""
     b, x, q = bufs
     b.copy_(b0)
     x.copy_(x0)
@@ -365,7 +365,7 @@ def run_ours(args):
                    "max_upper": MAX_UPPER, "step": "one MAID run to the stop rule",
                    "l2": "flushed between timed runs (256 MB write)", "parallelism": f"replicas x{world}"},
         "maid": {"time_to_tolerance_s": tot_ms_max / args.steps / 1e3,
-                 "form": "device-resident run: one CUDA graph of up to max_upper cooperative launches",
+                 "form": "device-resident run: one cooperative launch runs all upper iterations (a CUDA graph of one kernel node)",
                  "host_stepped_s": statistics.median(hs_ms) / 1e3,
                  "plain_gpu_maid_s": pms / 1e3, "speedup_vs_plain": pms / (tot_ms_max / args.steps),
                  "upper_iters_per_run": ups / args.steps, "accepted_per_run": accepted / args.steps,
@@ -380,7 +380,7 @@ def run_ours(args):
                      "flops_basis": "2 K^2 C H W per convolution pass, passes counted on the device"},
         "e2e": {"value": e2e_units / (e2e_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * MAX_UPPER,
+        "gpu_launches": args.steps,            # one cooperative launch per MAID run
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -398,7 +398,7 @@ def committed_traffic(upper_iters):
     """DRAM bytes per launch of the MAID kernel from the committed ncu summary,
     or None when the kernel sources changed since it was taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "maid_step_rgb256_k15_traffic.json")
+    path = os.path.join(ROOT, "profiles", "maid_run_rgb256_k15_traffic.json")
     try:
         rec = json.load(open(path))
     except Exception:
@@ -412,6 +412,94 @@ def committed_traffic(upper_iters):
     return rec.get("dram_bytes_per_launch")
 
 
+def run_batch64(args):
+    """The batch workload: 64 independent RGB problems of uneven size
+    (128^2..512^2) and kernel size (5..31), one MAID run each to the stop rule.
+    Timed two ways on the same inputs: one problem at a time (a device-resident
+    graph run per problem) and all problems in one batched graph run (one
+    cooperative launch per upper iteration for all of them; group sizes from
+    the balancer after two warm-up steps).  Prints one JSON line."""
+    import numpy as np
+    import torch
+    from paper_2502_09758_gb300 import adp, synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    insts = synth.batch_mixed(64, seed=0)
+    probs, ys, as_ = [], [], []
+    for inst in insts:
+        C, H, W = inst.shape
+        y = torch.tensor(inst.y, dtype=torch.float32, device=dev)
+        a = torch.tensor(inst.a, dtype=torch.float32, device=dev)
+        probs.append(adp.Problem(adp.Params(C, H, W, inst.K, alpha=1e-2, reg_param=1e-2, beta=0.3), y, a))
+        ys.append(y)
+        as_.append(a)
+    values = sum(int(np.prod(i.shape)) for i in insts)
+
+    def fresh():
+        st = [p.maid_init(eps=EPS0, delta=EPS0, step=STEP0, eps_stop=EPS_STOP) for p in probs]
+        return st, [a.clone() for a in as_], [y.clone() for y in ys], [torch.zeros_like(y) for y in ys]
+
+    # one problem at a time
+    singles = [adp.Batch([p]) for p in probs]
+    seq_ms, seq_iters = [], 0
+    for rep in range(2):
+        st, b, x, q = fresh()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it = 0
+        for i, bt in enumerate(singles):
+            (f, _, _, _), = bt.maid_run_graph([st[i]], [b[i]], [x[i]], [q[i]], MAX_UPPER)
+            it += f
+        torch.cuda.synchronize()
+        seq_ms.append((time.perf_counter() - t0) * 1e3)
+        seq_iters = it
+    # all problems in one batched launch per step
+    batch = adp.Batch(probs)
+    g0 = batch.group_sizes()
+    st, b, x, q = fresh()
+    for _ in range(2):                  # balancer warm-up on scratch state
+        batch.maid_step(st, b, x, q)
+    g1 = batch.group_sizes()
+    bat_ms, bat_iters = [], 0
+    for rep in range(2):
+        st, b, x, q = fresh()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tot = batch.maid_run_graph(st, b, x, q, MAX_UPPER)
+        torch.cuda.synchronize()
+        bat_ms.append((time.perf_counter() - t0) * 1e3)
+        bat_iters = sum(t[0] for t in tot)
+    line = {"metric": METRIC, "workload": "batch64_rgb_128-512_k5-31", "unit": UNIT, "n_problems": len(probs),
+            "values": values, "dtype": "f32", "data": "synthetic",
+            "sequential": {"ms": min(seq_ms), "fused_iters": seq_iters,
+                           "value": values / len(probs) * seq_iters / (min(seq_ms) / 1e3) / 1e6},
+            "batched": {"ms": min(bat_ms), "fused_iters": bat_iters,
+                        "value": values / len(probs) * bat_iters / (min(bat_ms) / 1e3) / 1e6,
+                        "ctas_initial": sum(g0), "group_sizes_initial_minmax": [min(g0), max(g0)],
+                        "group_sizes_balanced_minmax": [min(g1), max(g1)]},
+            "speedup_batched_vs_sequential": min(seq_ms) / min(bat_ms),
+            "note": "value uses the mean problem size (values/n) per fused iteration"}
+    print(json.dumps(line), flush=True)
+
+
+def run_profile_case(args):
+    """A short fixed program for profiler captures: problem creation, then three
+    lower-level launches of 4 FISTA iterations each (no timing, no JSON)."""
+    import torch
+    from paper_2502_09758_gb300 import adp, synth
+    inst = synth.WORKLOADS[args.profile_case](0)
+    C, H, W = inst.shape
+    y = torch.tensor(inst.y, dtype=torch.float32, device="cuda")
+    a = torch.tensor(inst.a, dtype=torch.float32, device="cuda")
+    prob = adp.Problem(adp.Params(C, H, W, inst.K, alpha=1e-2, reg_param=1e-2, beta=0.3), y, a)
+    for _ in range(3):
+        x = y.clone()
+        prob.lower_solve(a, x, 0.0, 4)
+    torch.cuda.synchronize()
+    print(f"profile case {args.profile_case}: last launch {prob.last_kernel_ms():.3f} ms")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -420,7 +508,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="rgb256_k15", choices=["rgb256_k15", "batch64"],
+                    help="batch64: the 64-problem batch, batched vs one at a time (not the headline line)")
+    ap.add_argument("--profile-case", default=None, choices=["rgb256_k15_motion", "rgb512_k31_gauss_perturbed",
+                                                              "rgb2048_k63_motion_gauss"],
+                    help="run a short fixed lower-level program for profiler captures")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
+    if args.workload == "batch64":
+        run_batch64(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

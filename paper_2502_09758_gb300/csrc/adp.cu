@@ -37,6 +37,17 @@ static thread_local char g_err[512];
 namespace adp {
 // lets the other translation units of the library report through adp_last_error
 void record_error(const char *msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+
+// Opts kernel fn in to all the dynamic shared memory its static part leaves
+// (the attribute is shared by every problem on the device, so it is the
+// device maximum rather than one problem's size).
+cudaError_t optin_dynamic_smem(const void *fn, int maxsmem)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem - (int)fa.sharedSizeBytes);
+}
 } // namespace adp
 
 static adp_status set_err(adp_status s, const char *fmt, const char *a = "", long long v = 0)
@@ -274,7 +285,7 @@ adp_status adp_problem_create(const adp_params *prm, const void *y, const void *
     int nw = MAXNW, total = 0;
     for (; nw >= 2; nw -= 2) {   // warps work in pairs
         total = q.prec == ADP_F32 ? Layout<float>(q.C, q.K, nw, g.wsm).total : Layout<double>(q.C, q.K, nw, g.wsm).total;
-        if ((size_t)total * p->esize + 5 * 1024 <= (size_t)maxsmem) break;
+        if ((size_t)total * p->esize + SMEM_STATIC_MARGIN <= (size_t)maxsmem) break;
     }
     if (nw < 2) {
         adp_problem_destroy(p);
@@ -287,7 +298,7 @@ adp_status adp_problem_create(const adp_params *prm, const void *y, const void *
     // rather than this problem's size: the attribute is shared by every problem
     // on the device, and a smaller value set for a later problem with a smaller
     // K would make launches of an earlier, larger problem fail
-    CKC(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem - 5 * 1024));
+    CKC(optin_dynamic_smem(kfn, maxsmem));
     int occ = 0;
     CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, 32 * nw, p->smem));
     if (occ < 1) {
@@ -589,7 +600,7 @@ static void batch_partition(adp_batch *bt)
 
 template <typename T>
 static void batch_fill(adp_batch *bt, const adp_maid_state *st, void *const *b, void *const *x, void *const *q,
-                       bool resident)
+                       bool resident, int max_steps)
 {
     for (int i = 0; i < bt->n; ++i) {
         adp_problem *p = bt->ps[i];
@@ -614,6 +625,7 @@ static void batch_fill(adp_batch *bt, const adp_maid_state *st, void *const *b, 
         mi.ll_max_iters = s->ll_max_iters; mi.cg_max_iters = s->cg_max_iters; mi.k = s->k; mi.halted = 0;
         j.maid_home = resident ? (MaidIn *)((unsigned char *)bt->djob + i * bt->job_bytes + offsetof(Job<T>, maid))
                                : nullptr;
+        j.max_steps = resident ? max_steps : 0;
         memcpy(bt->hjob + i * bt->job_bytes, &j, sizeof j);
     }
 }
@@ -645,6 +657,31 @@ static adp_status batch_report(adp_batch *bt, adp_maid_state *st, const MaidIn *
             first_bad = set_err(ADP_ELSFAIL, "MAID backtracking rounds exhausted for problem %s%lld", "", i);
     }
     return first_bad;
+}
+
+// balancer: a group's CTA-time (device time x CTAs) estimates its work for the
+// next launch; half the old estimate, half the measurement (both normalised)
+static void batch_rebalance(adp_batch *bt)
+{
+    bool any = false;
+    std::vector<double> w(bt->n);
+    for (int i = 0; i < bt->n; ++i) {
+        const double t = (double)(bt->hout[i].t_end - bt->hout[i].t_start);
+        const int gsz = bt->first[i + 1] - bt->first[i];
+        w[i] = t > 0 ? t * gsz : 0.0;
+        if (w[i] > 0) any = true;
+    }
+    if (any) {
+        double mn = 1e300, sw = 0.0, so = 0.0;
+        for (int i = 0; i < bt->n; ++i) if (w[i] > 0) mn = std::min(mn, w[i]);
+        for (int i = 0; i < bt->n; ++i) {
+            if (w[i] <= 0) w[i] = mn;
+            sw += w[i];
+            so += bt->work[i];
+        }
+        for (int i = 0; i < bt->n; ++i) bt->work[i] = 0.5 * bt->work[i] / so + 0.5 * w[i] / sw;
+        batch_partition(bt);
+    }
 }
 
 // One batched launch.  A batch of one problem launches the single-problem
@@ -725,7 +762,7 @@ adp_status adp_batch_create(adp_problem *const *ps, int n, adp_batch **out)
     CKB(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ps[0]->device));
     CKB(cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ps[0]->device));
     const void *fn = bt->prec == ADP_F32 ? kernel_f32_batched() : kernel_f64_batched();
-    CKB(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem - 5 * 1024));
+    CKB(optin_dynamic_smem(fn, maxsmem));
     int occ = 0;
     CKB(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * nw, smem));
     bt->max_ctas = occ * nsm;
@@ -786,8 +823,8 @@ adp_status adp_batch_maid_step(adp_batch *bt, adp_maid_state *st, void *const *b
     }
     cudaStream_t stream = bt->ps[0]->stream;
     CK(cudaSetDevice(bt->ps[0]->device));
-    if (bt->prec == ADP_F32) batch_fill<float>(bt, st, b, x, q, false);
-    else batch_fill<double>(bt, st, b, x, q, false);
+    if (bt->prec == ADP_F32) batch_fill<float>(bt, st, b, x, q, false, 0);
+    else batch_fill<double>(bt, st, b, x, q, false, 0);
     CK(cudaMemcpyAsync(bt->dctx, bt->hctx, bt->n * bt->ctx_bytes, cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(bt->djob, bt->hjob, bt->n * bt->job_bytes, cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(bt->dfirst, bt->first.data(), (bt->n + 1) * sizeof(int), cudaMemcpyHostToDevice, stream));
@@ -799,29 +836,10 @@ adp_status adp_batch_maid_step(adp_batch *bt, adp_maid_state *st, void *const *b
     CK(cudaStreamSynchronize(stream));
     CK(cudaEventElapsedTime(&bt->last_ms, bt->ev0, bt->ev1));
     const adp_status rs = batch_report(bt, st, nullptr);
-    // balancer: a group's CTA-time is its work estimate for the next step
-    bool any = false;
-    std::vector<double> w(bt->n);
-    for (int i = 0; i < bt->n; ++i) {
-        const double t = (double)(bt->hout[i].t_end - bt->hout[i].t_start);
-        const int gsz = bt->first[i + 1] - bt->first[i];
-        w[i] = t > 0 ? t * gsz : 0.0;
-        if (w[i] > 0) any = true;
-    }
-    if (any) {
-        double mn = 1e300, sw = 0.0, so = 0.0;
-        for (int i = 0; i < bt->n; ++i) if (w[i] > 0) mn = std::min(mn, w[i]);
-        for (int i = 0; i < bt->n; ++i) {
-            if (w[i] <= 0) w[i] = mn;
-            sw += w[i];
-            so += bt->work[i];
-        }
-        // half the old estimate, half the measurement (both normalised)
-        for (int i = 0; i < bt->n; ++i) bt->work[i] = 0.5 * bt->work[i] / so + 0.5 * w[i] / sw;
-        batch_partition(bt);
-    }
+    batch_rebalance(bt);
     return rs;
 }
+
 
 adp_status adp_batch_maid_run_graph(adp_batch *bt, adp_maid_state *st, void *const *b, void *const *x,
                                     void *const *q, int max_steps, long long *totals)
@@ -831,8 +849,8 @@ adp_status adp_batch_maid_run_graph(adp_batch *bt, adp_maid_state *st, void *con
         if (!b[i] || !x[i] || !q[i]) return set_err(ADP_EINVAL, "null data pointer for problem %s%lld", "", i);
     cudaStream_t stream = bt->ps[0]->stream;
     CK(cudaSetDevice(bt->ps[0]->device));
-    if (bt->prec == ADP_F32) batch_fill<float>(bt, st, b, x, q, true);
-    else batch_fill<double>(bt, st, b, x, q, true);
+    if (bt->prec == ADP_F32) batch_fill<float>(bt, st, b, x, q, true, max_steps);
+    else batch_fill<double>(bt, st, b, x, q, true, max_steps);
     CK(cudaMemcpyAsync(bt->dctx, bt->hctx, bt->n * bt->ctx_bytes, cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(bt->djob, bt->hjob, bt->n * bt->job_bytes, cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(bt->dfirst, bt->first.data(), (bt->n + 1) * sizeof(int), cudaMemcpyHostToDevice, stream));
@@ -858,7 +876,7 @@ adp_status adp_batch_maid_run_graph(adp_batch *bt, adp_maid_state *st, void *con
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(bt->cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            for (int s = 0; s < max_steps && res == ADP_OK; ++s) res = batch_launch(bt, bt->cs);
+            res = batch_launch(bt, bt->cs);   // one launch runs up to max_steps upper iterations per problem
             cudaError_t e2 = cudaStreamEndCapture(bt->cs, &graph);
             if (res == ADP_OK && e2 != cudaSuccess)
                 res = set_err(ADP_ECUDA, "graph capture: %s%lld", cudaGetErrorString(e2), 0);
@@ -902,6 +920,7 @@ adp_status adp_batch_maid_run_graph(adp_batch *bt, adp_maid_state *st, void *con
     for (int i = 0; i < bt->n; ++i) {
         st[i].stopped = (st[i].eps_stop > 0 && st[i].eps <= st[i].eps_stop) || state[i].halted;
     }
+    batch_rebalance(bt);
     return rs;
 }
 

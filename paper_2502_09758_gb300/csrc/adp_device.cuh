@@ -14,6 +14,7 @@ constexpr int MAXNW = 8;           // most warps per CTA
 constexpr int MAXC = 64;           // channels supported (per-channel step cache)
 constexpr int KMAX = 63;           // largest odd kernel size supported
 constexpr int NSLOT = 8;           // scalar reduction slots
+constexpr int SMEM_STATIC_MARGIN = 8 * 1024;   // static shared memory of the kernels is below this
 constexpr int QB = 8;              // lag columns per lane in the kernel-gradient correlation
 
 // Output rows per thread (a warp owns a strip of 32 columns x MR rows) and
@@ -555,6 +556,7 @@ struct Job {
     MaidIn *maid_home; // MAID: where the updated state is written back (device-resident runs), or null
     double eps, delta;
     int max_iters, flag;
+    int max_steps;    // MAID: upper iterations in this launch (<= 1: one)
     MaidIn maid;
 };
 

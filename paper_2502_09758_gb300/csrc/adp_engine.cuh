@@ -49,6 +49,7 @@ __shared__ int g_sflag;
 // so that it occupies no registers while the solves run).
 struct MaidRep {
     int ll_iters, cg_iters, ll_capped, cg_capped, trials;
+    long long fused;             // FISTA + CG iterations over the run
     double loss, gxn, znorm, psi;
 };
 __shared__ MaidRep g_rep;
@@ -62,6 +63,7 @@ struct Eng {
     static constexpr int NX = PC + MR - 1;
     static constexpr int EWB = 4;  // element-wise phases: loads issued per batch per thread
     const Ctx<T> &cx;
+    const Ctx<T> *mc;              // where the tensor maps live (parameter or global space)
     const T *wF, *wT;              // kernel orientations in use (shared memory or a global slot)
     T *wsm;                        // shared-memory home of both orientations (when cx.wsm)
     T *sb0;                        // this warp's region: stage buffers, halo-1 tiles, interior tile, mbarriers
@@ -95,8 +97,8 @@ struct Eng {
     __device__ int off() const { return cx.r4 - cx.r; }
     __device__ int ns() const { return cx.Kp / PC; }
 
-    __device__ Eng(const Ctx<T> &c, int nblk_, int bid_, unsigned char *smem)
-        : cx(c), mph(0), wslot(1), nblk(nblk_), bid(bid_), epoch(0), alive(true), tmafail(false), gedge(true)
+    __device__ Eng(const Ctx<T> &c, const Ctx<T> *maps, int nblk_, int bid_, unsigned char *smem)
+        : cx(c), mc(maps), mph(0), wslot(1), nblk(nblk_), bid(bid_), epoch(0), alive(true), tmafail(false), gedge(true)
     {
         lane = threadIdx.x & 31;
         warp = threadIdx.x >> 5;
@@ -177,17 +179,17 @@ struct Eng {
     // columns from image column col0 - r4; rows outside the padded image read 0.
     __device__ void box_s(T *dst, int b, int c, int row0, int col0, int trow, uint64_t *mb) const
     {
-        tma_load_4d(dst, &cx.map_s, col0 - cx.r4 + cx.Gx, row0 - cx.r + cx.Gy + trow, c, b, mb);
+        tma_load_4d(dst, &mc->map_s, col0 - cx.r4 + cx.Gx, row0 - cx.r + cx.Gy + trow, c, b, mb);
     }
     // halo-1 tile: rows row0-1 .. row0+MR, columns col0-4 .. col0+35 (pitch 40)
     __device__ void box_1(T *dst, int b, int c, int row0, int col0, uint64_t *mb) const
     {
-        tma_load_4d(dst, &cx.map_1, col0 - 4 + cx.Gx, row0 - 1 + cx.Gy, c, b, mb);
+        tma_load_4d(dst, &mc->map_1, col0 - 4 + cx.Gx, row0 - 1 + cx.Gy, c, b, mb);
     }
     // interior: rows row0 .. row0+MR-1, columns col0 .. col0+31 (pitch 32)
     __device__ void box_i(T *dst, int b, int c, int row0, int col0, uint64_t *mb) const
     {
-        tma_load_4d(dst, &cx.map_i, col0 + cx.Gx, row0 + cx.Gy, c, b, mb);
+        tma_load_4d(dst, &mc->map_i, col0 + cx.Gx, row0 + cx.Gy, c, b, mb);
     }
     __device__ unsigned bytes_s() const { return (unsigned)(cx.BW * NX * sizeof(T)); }
     __device__ static constexpr unsigned bytes_1() { return (unsigned)(40 * (MR + 2) * sizeof(T)); }
@@ -991,12 +993,15 @@ struct Eng {
     }
 
     // ------------------------------------------------------------ MAID
-    // One upper iteration of Algorithm 2; every CTA runs the same control flow
-    // on identical reduction results.  x~(b_k) is imported into B_XK; the trial
-    // solutions go to B_XT.  Register economy: the run's constant parameters
-    // are read from the job (or its device-resident home) where used, the
-    // report is accumulated in shared memory by thread 0, and only the
-    // adaptive quantities and the current comparison terms stay in registers.
+    // Upper iterations of Algorithm 2: one (jb.max_steps <= 1) or a whole run
+    // of up to jb.max_steps in this launch, stopping at the stop rule or when
+    // a step exhausts its backtracking rounds.  Every CTA runs the same control
+    // flow on identical reduction results.  x~(b_k) lives in B_XK between the
+    // steps; the trial solutions go to B_XT.  Register economy: the run's
+    // constant parameters are read from the job (or its device-resident home)
+    // where used, the report is accumulated in shared memory by thread 0, and
+    // only the adaptive quantities and the current comparison terms stay in
+    // registers.
     __device__ void maid(const Job<T> &jb)
     {
         const MaidIn &M = jb.maid_home ? *jb.maid_home : jb.maid;   // constant fields
@@ -1005,96 +1010,115 @@ struct Eng {
         int k = M.k;
         T *b = jb.bio;
         const int CKK = cx.C * cx.K * cx.K;
+        const int steps = jb.max_steps > 1 ? jb.max_steps : 1;
         long long passes = 0;
         bool stopped = (M.eps_stop > 0.0 && eps <= M.eps_stop) || M.halted;   // stop rule of Sec. 4.2
-        bool accepted = false;
-        int rounds = 0;
+        bool halted = false, any_accepted = false, accepted = false;
+        int rounds = 0, ran = 0, n_accepted = 0;
         if (tid() == 0) R = MaidRep{};
         __syncthreads();
         if (!stopped) {
             import_dense(jb.x, B_XK);
             if (!sync()) stopped = true;
         }
-        int j = M.max_bt;
-        for (int round = 0; round < M.max_rounds && alive && !stopped; ++round, ++j) {
-            rounds = round + 1;
-            // InexactGradient(b_k, eps_k, delta_k)
-            double gn = 0.0, res = 0.0;
-            int it = lower_solve(b, B_XK, B_XK, eps, M.ll_max_iters, gn, passes);
-            if (tid() == 0) { R.ll_iters += it; if (gn > eps) R.ll_capped = 1; }
-            if (!sync()) break;
-            double l0 = 0.0, gx0 = 0.0;
-            upper_loss(b, B_XK, l0, gx0, passes);
-            if (!alive) break;
-            int capped = 0;
-            it = cg(b, B_XK, B_G, delta, M.cg_max_iters, true, res, capped, passes);
-            if (tid() == 0) { R.cg_iters += it; if (capped) R.cg_capped = 1; }
-            if (!alive) break;
-            if (!sync()) break;
-            const double zz = cross(b, B_XK, B_Q, cx.ZK, true, true, passes);
-            if (!alive) break;
-            if (tid() == 0) R.znorm = sqrt(zz);
-            if (!isfinite(zz)) {
-                if (tid() == 0) raise(ST_NONFINITE);
-                alive = false;
-                break;
-            }
-            bool done = false;
-            for (int i = 0; i < j; ++i) {
-                if (tid() == 0) ++R.trials;
-                // b' = b - step z
-                for (long long e = gstart(); e < CKK; e += gstride())
-                    cx.BT[e] = (T)((double)__ldcg(b + e) - step * (double)__ldcg(cx.ZK + e));
+        for (int sidx = 0; sidx < steps && alive && !stopped && !halted; ++sidx) {
+            accepted = false;
+            rounds = 0;
+            // a step that exhausts its rounds leaves x~ as it was (the solves
+            // refine B_XK in place): keep a copy when a later step can fail
+            if (steps > 1) copy_buf(B_IN1, -1, B_XK);
+            if (tid() == 0) { R.ll_iters = R.cg_iters = R.ll_capped = R.cg_capped = R.trials = 0; }
+            int j = M.max_bt;
+            for (int round = 0; round < M.max_rounds && alive && !stopped; ++round, ++j) {
+                rounds = round + 1;
+                // InexactGradient(b_k, eps_k, delta_k)
+                double gn = 0.0, res = 0.0;
+                int it = lower_solve(b, B_XK, B_XK, eps, M.ll_max_iters, gn, passes);
+                if (tid() == 0) { R.ll_iters += it; R.fused += it; if (gn > eps) R.ll_capped = 1; }
                 if (!sync()) break;
-                double g1 = 0.0;
-                it = lower_solve(cx.BT, B_XK, B_XT, eps, M.ll_max_iters, g1, passes);
-                if (tid() == 0) { R.ll_iters += it; if (g1 > eps) R.ll_capped = 1; }
-                if (!sync()) break;
-                double l1 = 0.0, gx1 = 0.0;
-                upper_loss(cx.BT, B_XT, l1, gx1, passes);
+                double l0 = 0.0, gx0 = 0.0;
+                upper_loss(b, B_XK, l0, gx0, passes);
                 if (!alive) break;
-                // psi of Eq. 3.4 with eps_bar = eps_k
-                const double eb = eps;
-                const double psi = l1 + gx1 * eb + 0.5 * M.L_gx * eb * eb - l0 + gx0 * eb + M.lambda * step * zz;
-                if (tid() == 0) R.psi = psi;
-                if (psi <= 0.0) {
-                    for (long long e = gstart(); e < CKK; e += gstride()) b[e] = __ldcg(cx.BT + e);
-                    copy_buf(B_XK, -1, B_XT);
-                    if (tid() == 0) { R.loss = l1; R.gxn = gx1; }
-                    eps *= M.nu_up;
-                    delta *= M.nu_up;
-                    step *= M.rho_up;
-                    k += 1;
-                    accepted = true;
-                    done = true;
+                int capped = 0;
+                it = cg(b, B_XK, B_G, delta, M.cg_max_iters, true, res, capped, passes);
+                if (tid() == 0) { R.cg_iters += it; R.fused += it; if (capped) R.cg_capped = 1; }
+                if (!alive) break;
+                if (!sync()) break;
+                const double zz = cross(b, B_XK, B_Q, cx.ZK, true, true, passes);
+                if (!alive) break;
+                if (tid() == 0) R.znorm = sqrt(zz);
+                if (!isfinite(zz)) {
+                    if (tid() == 0) raise(ST_NONFINITE);
+                    alive = false;
                     break;
                 }
-                step *= M.rho_down;
+                bool done = false;
+                for (int i = 0; i < j; ++i) {
+                    if (tid() == 0) ++R.trials;
+                    // b' = b - step z
+                    for (long long e = gstart(); e < CKK; e += gstride())
+                        cx.BT[e] = (T)((double)__ldcg(b + e) - step * (double)__ldcg(cx.ZK + e));
+                    if (!sync()) break;
+                    double g1 = 0.0;
+                    it = lower_solve(cx.BT, B_XK, B_XT, eps, M.ll_max_iters, g1, passes);
+                    if (tid() == 0) { R.ll_iters += it; R.fused += it; if (g1 > eps) R.ll_capped = 1; }
+                    if (!sync()) break;
+                    double l1 = 0.0, gx1 = 0.0;
+                    upper_loss(cx.BT, B_XT, l1, gx1, passes);
+                    if (!alive) break;
+                    // psi of Eq. 3.4 with eps_bar = eps_k
+                    const double eb = eps;
+                    const double psi = l1 + gx1 * eb + 0.5 * M.L_gx * eb * eb - l0 + gx0 * eb + M.lambda * step * zz;
+                    if (tid() == 0) R.psi = psi;
+                    if (psi <= 0.0) {
+                        for (long long e = gstart(); e < CKK; e += gstride()) b[e] = __ldcg(cx.BT + e);
+                        copy_buf(B_XK, -1, B_XT);
+                        if (tid() == 0) { R.loss = l1; R.gxn = gx1; }
+                        eps *= M.nu_up;
+                        delta *= M.nu_up;
+                        step *= M.rho_up;
+                        k += 1;
+                        accepted = true;
+                        done = true;
+                        break;
+                    }
+                    step *= M.rho_down;
+                }
+                if (done || !alive) break;
+                if (tid() == 0) { R.loss = l0; R.gxn = gx0; }
+                eps *= M.nu_down;
+                delta *= M.nu_down;
+                if (M.eps_stop > 0.0 && eps <= M.eps_stop) stopped = true;
             }
-            if (done || !alive) break;
-            if (tid() == 0) { R.loss = l0; R.gxn = gx0; }
-            eps *= M.nu_down;
-            delta *= M.nu_down;
-            if (M.eps_stop > 0.0 && eps <= M.eps_stop) stopped = true;
+            if (!alive) break;
+            ++ran;
+            if (accepted) {
+                any_accepted = true;
+                ++n_accepted;
+                // the next step reads b_{k+1}, written above by other CTAs
+                if (sidx + 1 < steps && !sync()) break;
+            } else if (!stopped) {
+                halted = true;         // a step exhausted its rounds: the run ends here
+            }
         }
         // x~ and q back to the caller (x unchanged unless a step was accepted)
-        if (alive && rounds > 0 && sync()) {
-            if (accepted) export_dense(B_XK, (T *)jb.x);
+        if (alive && ran > 0 && sync()) {
+            if (any_accepted) export_dense(halted ? B_IN1 : B_XK, (T *)jb.x);
             export_dense(B_Q, jb.q);
         }
         __syncthreads();               // thread 0's report entries are complete
         if (tid() == 0 && bid == 0) {
-            if (jb.maid_home) {        // device-resident state for the next launch (same bytes when unchanged)
+            if (jb.maid_home) {        // device-resident state for a later launch (same bytes when unchanged)
                 MaidIn *h = jb.maid_home;
                 h->eps = eps; h->delta = delta; h->step = step; h->k = k;
-                if (rounds > 0 && !accepted && !stopped && alive) h->halted = 1;
+                if (halted && alive) h->halted = 1;
             }
-            if (cx.totals && rounds > 0) {
+            if (cx.totals && ran > 0) {
                 MaidTotals *t = cx.totals;
-                t->fused_iters += R.ll_iters + R.cg_iters;
+                t->fused_iters += R.fused;
                 t->conv_passes += passes;
-                t->upper_iters += 1;
-                t->accepted += accepted ? 1 : 0;
+                t->upper_iters += ran;
+                t->accepted += n_accepted;
             }
             DevOut *o = cx.out;
             o->accepted = accepted; o->rounds = rounds; o->trials = R.trials;
@@ -1102,6 +1126,7 @@ struct Eng {
             o->k = k; o->eps = eps; o->delta = delta; o->step = step;
             o->loss = R.loss; o->gradx_norm = R.gxn; o->znorm = R.znorm; o->psi = R.psi;
             o->conv_passes = passes; o->stopped = stopped;
+            o->iters = ran;
         }
     }
 };
@@ -1215,7 +1240,7 @@ __global__ void __launch_bounds__(MAXNW * 32, 1) adp_kernel(const __grid_constan
         return;
     }
     if (threadIdx.x == 0 && blockIdx.x == 0) cx.out->t_start = (long long)globaltimer_ns();
-    Eng<T> e(cx, gridDim.x, blockIdx.x, smem_raw);
+    Eng<T> e(cx, &cx, gridDim.x, blockIdx.x, smem_raw);
     run_program<T>(e, cx, jb);
     if (threadIdx.x == 0 && blockIdx.x == 0) cx.out->t_end = (long long)globaltimer_ns();
 }
@@ -1232,13 +1257,19 @@ __global__ void __launch_bounds__(MAXNW * 32, 1) adp_kernel_batched(const Ctx<T>
     int g = 0;
     while (g + 1 < n && (int)blockIdx.x >= __ldg(first + g + 1)) ++g;
     const int f0 = __ldg(first + g), nb = __ldg(first + g + 1) - f0;
-    const Ctx<T> &cx = ctxs[g];
+    // the record in shared memory (its fields are read all over the engine);
+    // the tensor maps are used from global memory, where TMA can read them
+    __shared__ __align__(64) unsigned char ctx_sh[sizeof(Ctx<T>)];
+    for (int i = threadIdx.x; i < (int)(sizeof(Ctx<T>) / 4); i += blockDim.x)
+        reinterpret_cast<int *>(ctx_sh)[i] = __ldg(reinterpret_cast<const int *>(ctxs + g) + i);
+    __syncthreads();
+    const Ctx<T> &cx = *reinterpret_cast<const Ctx<T> *>(ctx_sh);
     if ((reinterpret_cast<uintptr_t>(smem_raw) & 127) != 0) {
         if (threadIdx.x == 0) atomicCAS(&cx.out->status, ST_OK, ST_ALIGN);
         return;
     }
     if (threadIdx.x == 0 && blockIdx.x == (unsigned)f0) cx.out->t_start = (long long)globaltimer_ns();
-    Eng<T> e(cx, nb, (int)blockIdx.x - f0, smem_raw);
+    Eng<T> e(cx, ctxs + g, nb, (int)blockIdx.x - f0, smem_raw);
     run_program<T>(e, cx, jobs[g]);
     if (threadIdx.x == 0 && blockIdx.x == (unsigned)f0) cx.out->t_end = (long long)globaltimer_ns();
 }

@@ -26,6 +26,7 @@ namespace adp {
 const void *kernel_f32();
 const void *kernel_f64();
 void record_error(const char *msg);   // adp.cu: the message adp_last_error returns
+cudaError_t optin_dynamic_smem(const void *fn, int maxsmem);   // adp.cu
 } // namespace adp
 
 using namespace adp;
@@ -78,10 +79,8 @@ adp_status setup_device(int dev, DeviceSetup **out)
         if (cudaDeviceGetAttribute(&s.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&s.maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
             return fail(ADP_ECUDA, "device attribute query failed");
-        if (cudaFuncSetAttribute(kernel_f32(), cudaFuncAttributeMaxDynamicSharedMemorySize, s.maxsmem - 5 * 1024) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(kernel_f64(), cudaFuncAttributeMaxDynamicSharedMemorySize, s.maxsmem - 5 * 1024) !=
-                cudaSuccess)
+        if (optin_dynamic_smem(kernel_f32(), s.maxsmem) != cudaSuccess ||
+            optin_dynamic_smem(kernel_f64(), s.maxsmem) != cudaSuccess)
             return fail(ADP_ECUDA, "cudaFuncSetAttribute failed");
         s.scratch = (unsigned char *)ptr;
         s.ready = true;
@@ -109,7 +108,7 @@ adp_status run_noalloc(const adp_params &q, DeviceSetup &ds, const void *y, cons
     int total = 0, nw = MAXNW;
     for (; nw >= 2; nw -= 2) {   // warps work in pairs
         total = Layout<T>(q.C, q.K, nw, g.wsm).total;
-        if ((size_t)total * sizeof(T) + 5 * 1024 <= (size_t)ds.maxsmem) break;
+        if ((size_t)total * sizeof(T) + SMEM_STATIC_MARGIN <= (size_t)ds.maxsmem) break;
     }
     if (nw < 2) return fail(ADP_EINVAL, "kernel size too large for shared memory");
     const size_t smem = (size_t)total * sizeof(T);
