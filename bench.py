@@ -48,6 +48,25 @@ EPS0, STEP0 = 1e-4, 1e-6
 EPS_STOP = 5e-5        # stop rule (Sec. 4.2): near the FP32 floor of ||grad_x h|| at this size
 MAX_UPPER = 40         # cap on upper iterations per run
 
+# The other single-problem workloads (parity-test shapes, measured on request
+# with --workload; the headline line is the 256^2 one): synthetic instance,
+# element type, stop threshold (above the FP32 floor of ||grad_x h||, which
+# grows with the image size; the paper's 1e-6 for the FP64 64^2 case), upper
+# iteration cap, the oracle's bounded CPU sample (FISTA iterations, and a
+# centred crop of the image when the full image is too slow for one), and the
+# MAID start (eps_0 = delta_0, alpha_0) where it differs from the 256^2 one:
+# it must lie above the stop threshold, and the step shrinks with the image.
+WORKLOAD_SPECS = {
+    "rgb256_k15": dict(name="rgb256_k15_motion", fn="rgb256_k15", dtype="f32", eps_stop=5e-5, max_upper=40,
+                       cpu_iters=60, cpu_crop=None),
+    "gray64_k7": dict(name="gray64_k7_gauss_fp64", fn="gray64_k7", dtype="f64", eps_stop=1e-6, max_upper=50,
+                      cpu_iters=4000, cpu_crop=None),
+    "rgb512_k31": dict(name="rgb512_k31_gauss_perturbed", fn="rgb512_k31", dtype="f32", eps_stop=1e-4,
+                       max_upper=40, cpu_iters=6, cpu_crop=None, eps0=1e-3, step0=1e-6),
+    "rgb2048_k63": dict(name="rgb2048_k63_motion_gauss", fn="rgb2048_k63", dtype="f32", eps_stop=1e-3,
+                        max_upper=20, cpu_iters=2, cpu_crop=192, eps0=1e-2, step0=1e-7),
+}
+
 
 def peaks():
     try:
@@ -110,15 +129,21 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_sample(inst, iters):
+def oracle_sample(inst, iters, crop=None):
     """FP64 oracle (as it stands, single thread) running FISTA iterations of the
-    lower level on the same workload: returns (Mvalue*iter/s, seconds)."""
+    lower level on the same workload (or on a centred crop x crop window of it,
+    same kernel): returns (Mvalue*iter/s, seconds)."""
     import oracle
     oracle.build()
     C, H, W = inst.shape
+    y = inst.y
+    if crop:
+        i0, j0 = (H - crop) // 2, (W - crop) // 2
+        y = y[:, i0:i0 + crop, j0:j0 + crop].copy()
+        H = W = crop
     P = oracle.Problem(C, H, W, inst.K, alpha=1e-2, reg_param=1e-2, beta=0.3)
     t = time.perf_counter()
-    P.fista(inst.a, inst.y, inst.y, eps=0.0, max_iters=iters)
+    P.fista(inst.a, y, y, eps=0.0, max_iters=iters)
     dt = time.perf_counter() - t
     return C * H * W * iters / dt / 1e6, dt
 
@@ -210,7 +235,7 @@ def plain_maid_run(prob, a, y):
             z, _, _, _, _ = prob.hypergrad(b, x, delta, max_iters=s.cg_max_iters)
             zz = float((z.double() ** 2).sum())
             for _ in range(j):
-                bt = (b.double() - step * z.double()).float()
+                bt = (b.double() - step * z.double()).to(b.dtype)
                 xt = x.clone()
                 prob.lower_solve(bt, xt, eps, s.ll_max_iters)
                 l1, gx1 = prob.upper_loss(bt, xt)
@@ -264,13 +289,17 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    inst = synth.rgb256_k15(seed=rank)
+    spec = WORKLOAD_SPECS[args.workload]
+    inst = getattr(synth, spec["fn"])(seed=rank)
     C, H, W = inst.shape
     K = inst.K
     N = C * H * W
-    y = torch.tensor(inst.y, dtype=torch.float32, device=dev)
-    a = torch.tensor(inst.a, dtype=torch.float32, device=dev)
-    prob = adp.Problem(adp.Params(C, H, W, K, alpha=1e-2, reg_param=1e-2, beta=0.3), y, a)
+    f64 = spec["dtype"] == "f64"
+    tdt = torch.float64 if f64 else torch.float32
+    y = torch.tensor(inst.y, dtype=tdt, device=dev)
+    a = torch.tensor(inst.a, dtype=tdt, device=dev)
+    prob = adp.Problem(adp.Params(C, H, W, K, alpha=1e-2, reg_param=1e-2, beta=0.3,
+                                  prec=adp.ADP_F64 if f64 else adp.ADP_F32), y, a)
     batch = adp.Batch([prob])
     bufs = (torch.empty_like(a), torch.empty_like(y), torch.empty_like(y))
     for _ in range(args.warmup):
@@ -346,21 +375,23 @@ def run_ours(args):
         _ = float(st2.loss)
         e2e_ms += (time.perf_counter() - t0) * 1e3
         e2e_units += N * it
-    esz = 4
+    esz = 8 if f64 else 4
     h2d = (C * K * K + N) * esz
     d2h = (C * K * K + N) * esz + 8
 
     pk = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     peak_tf = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    if f64:                  # FP64 FMA: the nominal 1.25 TFLOP/s of GB300 (no measured figure)
+        peak_tf = 1.25
     flops = passes * 2.0 * K * K * N
     achieved = flops / (kern_ms / 1e3) / 1e12
     traffic = committed_traffic(ups)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "C": C, "H": H, "W": W, "K": K, "alpha": 1e-2, "huber": 1e-2,
+        "scaling": "weak", "vs_baseline": None, "dtype": spec["dtype"], "data": "synthetic",
+        "config": {"workload": spec["name"], "C": C, "H": H, "W": W, "K": K, "alpha": 1e-2, "huber": 1e-2,
                    "beta": 0.3, "maid_eps0": EPS0, "maid_step0": STEP0, "eps_stop": EPS_STOP,
                    "max_upper": MAX_UPPER, "step": "one MAID run to the stop rule",
                    "l2": "flushed between timed runs (256 MB write)", "parallelism": f"replicas x{world}"},
@@ -376,7 +407,8 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved / peak_tf, "traffic": traffic,
                      "kernel": "adp_kernel<float> (persistent MAID step, graph-replayed)",
-                     "peak_basis": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
+                     "peak_basis": ("nominal GB300 FP64 rate" if f64 else
+                                    f"152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"),
                      "flops_basis": "2 K^2 C H W per convolution pass, passes counted on the device"},
         "e2e": {"value": e2e_units / (e2e_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -384,10 +416,12 @@ def run_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt = oracle_sample(inst, args.cpu_iters)
+        iters_cpu = spec["cpu_iters"] if args.workload != "rgb256_k15" else args.cpu_iters
+        v, dt = oracle_sample(inst, iters_cpu, spec["cpu_crop"])
+        where = (f"a centred {spec['cpu_crop']}x{spec['cpu_crop']} crop (same kernel) of the {C}x{H}x{W}, K={K} workload"
+                 if spec["cpu_crop"] else f"the {C}x{H}x{W}, K={K} workload")
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{args.cpu_iters} FISTA iterations of the FP64 oracle on the "
-                                          f"{C}x{H}x{W}, K={K} workload ({dt:.1f} s)"}
+                                "sample": f"{iters_cpu} FISTA iterations of the FP64 oracle on {where} ({dt:.1f} s)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -508,8 +542,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="rgb256_k15", choices=["rgb256_k15", "batch64"],
-                    help="batch64: the 64-problem batch, batched vs one at a time (not the headline line)")
+    ap.add_argument("--workload", default="rgb256_k15", choices=list(WORKLOAD_SPECS) + ["batch64"],
+                    help="rgb256_k15 (default) is the headline line; the others measure the other workloads: "
+                         "batch64 the 64-problem batch, batched vs one at a time")
     ap.add_argument("--profile-case", default=None, choices=["rgb256_k15_motion", "rgb512_k31_gauss_perturbed",
                                                               "rgb2048_k63_motion_gauss"],
                     help="run a short fixed lower-level program for profiler captures")
@@ -520,6 +555,10 @@ def main():
     if args.workload == "batch64":
         run_batch64(args)
         return
+    global EPS_STOP, MAX_UPPER, EPS0, STEP0
+    spec = WORKLOAD_SPECS[args.workload]
+    EPS_STOP, MAX_UPPER = spec["eps_stop"], spec["max_upper"]
+    EPS0, STEP0 = spec.get("eps0", EPS0), spec.get("step0", STEP0)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
