@@ -274,6 +274,144 @@ def reduce_over_ranks(tot_ms, units, device=None):
     return float(tmax[0]), float(t[1])
 
 
+def torch_maid_run(inst, max_upper, dtype, dev):
+    """The same Algorithm 2 written with PyTorch tensor ops on the GPU (cuDNN
+    depthwise convolutions with circular padding, element-wise ops, host-side
+    control with a device sync per stopping test), the way the method is
+    written without this library.  Same readings as the library: h with 1/2,
+    Huber TV, FISTA with step 1/L_c and the stopping test on ||grad h(y_k)||,
+    CG from zero, z with the sign of Eq. 3.2, psi of Eq. 3.4, the stop rule.
+    Returns (wall ms, fused iterations, upper iterations, b, x)."""
+    import torch
+    import torch.nn.functional as F
+    torch.backends.cudnn.allow_tf32 = False
+    torch.backends.cuda.matmul.allow_tf32 = False
+    C, H, W = inst.shape
+    K = inst.K
+    r = (K - 1) // 2
+    alpha, gam, beta = 1e-2, 1e-2, 0.3
+    y = torch.tensor(inst.y, dtype=dtype, device=dev)[None]
+    a = torch.tensor(inst.a, dtype=dtype, device=dev)
+
+    def corr(x, w):                       # sum_pq w[c,p,q] x[c, i+p-r, j+q-r], periodic
+        return F.conv2d(F.pad(x, (r, r, r, r), mode="circular"), w[:, None], groups=C)
+
+    def B(b, x):                          # (b * x)[i,j] = sum b[p,q] x[i-p+r, j-q+r]
+        return corr(x, torch.flip(b, (1, 2)))
+
+    def Bt(b, z):
+        return corr(z, b)
+
+    def Dh(x): return torch.roll(x, -1, 3) - x
+    def Dv(x): return torch.roll(x, -1, 2) - x
+    def Dht(w): return torch.roll(w, 1, 3) - w
+    def Dvt(w): return torch.roll(w, 1, 2) - w
+    def dphi(t): return torch.clamp(t / gam, -1.0, 1.0)
+    def ddphi(t): return (t.abs() <= gam).to(t.dtype) / gam
+
+    def grad_h(b, x):
+        return Bt(b, B(b, x) - y) + alpha * (Dht(dphi(Dh(x))) + Dvt(dphi(Dv(x))))
+
+    def hess(b, x, v):
+        return Bt(b, B(b, v)) + alpha * (Dht(ddphi(Dh(x)) * Dh(v)) + Dvt(ddphi(Dv(x)) * Dv(v)))
+
+    def fista(b, x0, eps, cap=300):
+        l1 = b.abs().sum((1, 2)).double()
+        tau = (1.0 / (l1 * l1 + 8.0 * alpha / gam)).to(dtype)[None, :, None, None]
+        x, yk, t, it = x0.clone(), x0.clone(), 1.0, 0
+        while True:
+            g = grad_h(b, yk)
+            if float(torch.linalg.vector_norm(g.double())) <= eps or it >= cap:
+                return yk, it
+            xn = yk - tau * g
+            tn = (1.0 + (1.0 + 4.0 * t * t) ** 0.5) / 2.0
+            yk = xn + ((t - 1.0) / tn) * (xn - x)
+            x, t, it = xn, tn, it + 1
+
+    def upper(b, x):
+        e = B(a, x) - y
+        g = float((e.double() ** 2).sum())
+        gx = 2.0 * Bt(a, e)
+        d = b - a
+        dh = torch.zeros_like(d); dh[:, :, :-1] = d[:, :, 1:] - d[:, :, :-1]
+        dv = torch.zeros_like(d); dv[:, :-1, :] = d[:, 1:, :] - d[:, :-1, :]
+        rb = beta * float((d.double() ** 2).sum() + (dh.double() ** 2).sum() + (dv.double() ** 2).sum())
+        return g + rb, gx, float(torch.linalg.vector_norm(gx.double()))
+
+    def grad_r(b):
+        d = (b - a).double()
+        gd = d.clone()
+        dh = torch.zeros_like(d); dh[:, :, :-1] = d[:, :, 1:] - d[:, :, :-1]
+        dv = torch.zeros_like(d); dv[:, :-1, :] = d[:, 1:, :] - d[:, :-1, :]
+        gd = gd + torch.roll(dh, 1, 2) * (torch.arange(K, device=dev) > 0).double()[None, None] - dh
+        gd = gd + torch.roll(dv, 1, 1) * (torch.arange(K, device=dev) > 0).double()[None, :, None] - dv
+        return (2.0 * beta * gd).to(dtype)
+
+    def cg(b, x, rhs, delta, cap=1000):
+        q = torch.zeros_like(rhs); res = rhs.clone(); p = res.clone()
+        rr = float((res.double() ** 2).sum()); it = 0
+        while rr ** 0.5 > delta and it < cap:
+            hp = hess(b, x, p)
+            php = float((p.double() * hp.double()).sum())
+            if php <= 0: break
+            al = rr / php
+            q = q + al * p; res = res - al * hp
+            rn = float((res.double() ** 2).sum()); it += 1
+            if rn ** 0.5 <= delta: break
+            p = res + (rn / rr) * p; rr = rn
+        return q, it
+
+    def cross(b, x, q):                   # sum_ij x[i-p+r, j-q+r] (Bq)[i,j] + q[...] (Bx - y)[i,j]
+        u, v = B(b, q), B(b, x) - y
+        xp = F.pad(x, (r, r, r, r), mode="circular")
+        qp = F.pad(q, (r, r, r, r), mode="circular")
+        s1 = F.conv2d(xp, u[0][:, None], groups=C)        # (1, C, K, K): lag K-1-p, K-1-q
+        s2 = F.conv2d(qp, v[0][:, None], groups=C)
+        return torch.flip((s1 + s2)[0], (1, 2))
+
+    b = a.clone()
+    x = y.clone()
+    eps, delta, step = EPS0, EPS0, STEP0
+    L_gx = 2.0 * max(float(a[c].abs().sum()) ** 2 for c in range(C))
+    sync = torch.cuda.synchronize if y.is_cuda else (lambda: None)
+    sync()
+    t0 = time.perf_counter()
+    fused, ups = 0, 0
+    stopped = eps <= EPS_STOP
+    while ups < max_upper and not stopped:
+        ups += 1
+        accepted = False
+        j = 5
+        for _ in range(20):
+            x, it = fista(b, x, eps); fused += it
+            l0, gx, gx0 = upper(b, x)
+            q, it = cg(b, x, gx, delta); fused += it
+            z = -cross(b, x, q) + grad_r(b)
+            zz = float((z.double() ** 2).sum())
+            for _ in range(j):
+                bt = (b.double() - step * z.double()).to(dtype)
+                xt, it = fista(bt, x, eps); fused += it
+                l1, _, gx1 = upper(bt, xt)
+                psi = l1 + gx1 * eps + 0.5 * L_gx * eps * eps - l0 + gx0 * eps + 1e-4 * step * zz
+                if psi <= 0.0:
+                    b, x = bt, xt
+                    eps, delta, step = eps * 1.25, delta * 1.25, step * 1.1
+                    accepted = True
+                    break
+                step *= 0.5
+            if accepted:
+                break
+            eps, delta = eps * 0.5, delta * 0.5
+            j += 1
+            if eps <= EPS_STOP:
+                stopped = True
+                break
+        if not accepted:
+            break
+    sync()
+    return (time.perf_counter() - t0) * 1e3, fused, ups, b, x[0]
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -356,6 +494,13 @@ def run_ours(args):
     pxr = px.double().cpu().numpy()
     plain_psnr = 10 * np.log10(1.0 / np.mean((pxr - inst.x_true) ** 2))
 
+    # the same method written with PyTorch tensor ops (one run, after a warm one)
+    tms, tfused, tups, tb, tx = 0.0, 0, 0, None, None
+    if not args.no_torch_baseline:
+        torch_maid_run(inst, MAX_UPPER, tdt, dev)
+        tms, tfused, tups, tb, tx = torch_maid_run(inst, MAX_UPPER, tdt, dev)
+        torch_psnr = 10 * np.log10(1.0 / np.mean((tx.double().cpu().numpy() - inst.x_true) ** 2))
+
     # end to end through the public API with host buffers: per run, H2D of the
     # inputs (b_0, x_0) from pinned memory, the run, D2H of b, x~ and the loss
     b0_h = a.cpu().pin_memory()
@@ -399,6 +544,10 @@ def run_ours(args):
                  "form": "device-resident run: one cooperative launch runs all upper iterations (a CUDA graph of one kernel node)",
                  "host_stepped_s": statistics.median(hs_ms) / 1e3,
                  "plain_gpu_maid_s": pms / 1e3, "speedup_vs_plain": pms / (tot_ms_max / args.steps),
+                 "torch_maid_s": (tms / 1e3) if tms else None,
+                 "torch_maid_fused_iters": tfused or None, "torch_maid_upper_iters": tups or None,
+                 "torch_final_psnr_x_db": torch_psnr if tms else None,
+                 "speedup_vs_torch": (tms / (tot_ms_max / args.steps)) if tms else None,
                  "upper_iters_per_run": ups / args.steps, "accepted_per_run": accepted / args.steps,
                  "fused_iters_per_run": iters / args.steps, "eps_end": st.eps, "stopped": bool(st.stopped),
                  "final_psnr_x_db": psnr_x, "final_psnr_b_db": psnr_b, "plain_final_psnr_x_db": plain_psnr,
@@ -542,6 +691,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-torch-baseline", action="store_true",
+                    help="skip the MAID written with PyTorch tensor ops (reported beside the run)")
     ap.add_argument("--workload", default="rgb256_k15", choices=list(WORKLOAD_SPECS) + ["batch64"],
                     help="rgb256_k15 (default) is the headline line; the others measure the other workloads: "
                          "batch64 the 64-problem batch, batched vs one at a time")
