@@ -81,6 +81,24 @@ adp_status adp_apply_B(adp_problem *p, const void *b, const void *x, void *out);
 /* out = B^T z (the adjoint: correlation with b). */
 adp_status adp_apply_Bt(adp_problem *p, const void *b, const void *z, void *out);
 
+/* The same operators with BF16 operands and FP32 accumulation, on the tensor
+ * cores (the BF16-input precision of the operator applications of Eq. 2.4):
+ * x (or z) and b are rounded to BF16 (round to nearest even), every product
+ * of two BF16 values is exact in FP32, and the K^2 products of an output are
+ * summed in FP32 in tensor memory.  Only for ADP_F32 problems (float
+ * pointers) with K <= 33; otherwise ADP_EINVAL.  The first call allocates the
+ * operator's workspace (a BF16 copy of one image with periodic borders and
+ * the kernel's Toeplitz bands, about C*(H+K)*(W+K)*2 + C*K*4096 bytes), which
+ * the problem keeps until it is destroyed.  Each call runs three kernels on
+ * the problem's stream (kernel bands, image conversion, correlation);
+ * adp_last_kernel_ms reports the correlation alone and
+ * adp_bf16_prep_ms_last the two preparation kernels. */
+adp_status adp_apply_B_bf16(adp_problem *p, const void *b, const void *x, void *out);
+adp_status adp_apply_Bt_bf16(adp_problem *p, const void *b, const void *z, void *out);
+double adp_bf16_prep_ms_last(adp_problem *p);
+/* CTAs of the tensor-core correlation's launch (0 before the first call). */
+int adp_bf16_grid_size(adp_problem *p);
+
 /* out = grad_x h(x, b) = B^T(B x - y) + alpha grad J(x)   (Prop. 1, gradient);
  * *norm = ||out||_2 accumulated in FP64.  `out` may be NULL. */
 adp_status adp_grad_lower(adp_problem *p, const void *b, const void *x, void *out, double *norm);

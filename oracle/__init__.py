@@ -292,6 +292,18 @@ class Problem:
         return bool(acc), q
 
 
+def bf16_round(a) -> np.ndarray:
+    """Operands of the BF16-input operator: each value rounded first to FP32,
+    then to bfloat16 (1 sign, 8 exponent, 7 stored mantissa bits: FP32 with
+    the low 16 bits dropped) with round-to-nearest, ties to even, returned as
+    float64.  Written out on the FP32 bit pattern: add 0x7FFF plus the lowest
+    kept bit, then clear the low 16 bits (finite inputs only)."""
+    f = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64).reshape(f.shape)
+
+
 def norm(v) -> float:
     v = _f64(v).ravel()
     return _L().orc_norm(_ptr(v), v.size)

@@ -10,6 +10,7 @@
 // This file is the host side: argument checks, workspace, cooperative launches.
 // The kernels live in adp_engine.cuh, instantiated in adp_f32.cu / adp_f64.cu.
 #include "adp_device.cuh"
+#include "adp_tc.cuh"
 #include "adp.h"
 
 #include <cuda_runtime.h>
@@ -82,6 +83,8 @@ struct adp_problem {
     CUtensorMap map_s, map_1, map_i;
     cudaEvent_t ev0, ev1;  // bracket the cooperative launch on the problem's stream
     float last_ms;
+    TcPlan *tc;            // BF16 tensor-core operator workspace (made on first use)
+    TcTimes tc_times;
 };
 
 // ------------------------------------------------------------ tensor maps
@@ -130,6 +133,27 @@ int encode_tensor_maps(void *ws, int nbuf, int C, const Geom &g, int esize, int 
             snprintf(err, errlen, "tensor map encoding (%s box) failed with CUresult %d", m.name, (int)r);
             return 1;
         }
+    }
+    return 0;
+}
+} // namespace adp
+
+namespace adp {
+int encode_bf16_swizzled_3d(void *base, const unsigned long long dims[3], const unsigned long long strides[2],
+                            const unsigned box[3], CUtensorMap *map, char *err, int errlen)
+{
+    EncodeTiledFn fn = encode_fn(err, errlen);
+    if (!fn) return 1;
+    const cuuint64_t d[3] = {dims[0], dims[1], dims[2]};
+    const cuuint64_t st[2] = {strides[0], strides[1]};
+    const cuuint32_t bx[3] = {box[0], box[1], box[2]};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, d, st, bx, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        snprintf(err, errlen, "tensor map encoding (BF16 image) failed with CUresult %d", (int)r);
+        return 1;
     }
     return 0;
 }
@@ -231,6 +255,7 @@ void adp_problem_destroy(adp_problem *p)
     if (p->hout) cudaFreeHost(p->hout);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
+    tc_plan_destroy(p->tc);
     free(p->a_host);
     free(p);
 }
@@ -383,6 +408,46 @@ adp_status adp_apply_Bt(adp_problem *p, const void *b, const void *z, void *out)
     NEED(p, b, z, out);
     return dispatch_job(p, M_APPLY_BT, b, z, out, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, nullptr);
 }
+
+static adp_status apply_bf16(adp_problem *p, const void *b, const void *x, void *out, bool transpose)
+{
+    NEED(p, b, x, out);
+    if (p->prm.prec != ADP_F32) return set_err(ADP_EINVAL, "BF16 operator needs an ADP_F32 problem%s", "", 0);
+    if (p->prm.K > TC_KMAX) return set_err(ADP_EINVAL, "BF16 operator supports K <= 33%s (K = %lld)", "", p->prm.K);
+    CK(cudaSetDevice(p->device));
+    char emsg[256];
+    if (!p->tc) {
+        const int rc = tc_plan_create(p->prm.C, p->prm.H, p->prm.W, p->prm.K, p->device, &p->tc, emsg, sizeof emsg);
+        if (rc) {
+            record_error(emsg);
+            return rc == 1 ? ADP_EINVAL : rc == 2 ? ADP_ENOMEM : ADP_ECUDA;
+        }
+    }
+    int dst = ST_OK;
+    const long long timeout_ns = (long long)((p->prm.wait_timeout_s > 0 ? p->prm.wait_timeout_s : 2.0) * 1e9);
+    if (tc_apply(p->tc, (const float *)b, (const float *)x, (float *)out, transpose, timeout_ns, p->stream,
+                 &p->tc_times, &dst, emsg, sizeof emsg)) {
+        record_error(emsg);
+        return ADP_ECUDA;
+    }
+    p->last_ms = p->tc_times.corr_ms;
+    if (dst == ST_TIMEOUT) return set_err(ADP_ETIMEOUT, "device-side wait gave up%s", "", 0);
+    if (dst != ST_OK) return set_err(ADP_ECUDA, "unexpected device status%s %lld", "", dst);
+    return ADP_OK;
+}
+
+adp_status adp_apply_B_bf16(adp_problem *p, const void *b, const void *x, void *out)
+{
+    return apply_bf16(p, b, x, out, false);
+}
+
+adp_status adp_apply_Bt_bf16(adp_problem *p, const void *b, const void *z, void *out)
+{
+    return apply_bf16(p, b, z, out, true);
+}
+
+double adp_bf16_prep_ms_last(adp_problem *p) { return p && p->tc ? (double)p->tc_times.prep_ms : -1.0; }
+int adp_bf16_grid_size(adp_problem *p) { return p ? tc_grid(p->tc) : 0; }
 
 adp_status adp_grad_lower(adp_problem *p, const void *b, const void *x, void *out, double *norm)
 {

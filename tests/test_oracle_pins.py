@@ -477,3 +477,38 @@ def test_single_output_functions_match_whole_image(orc, reg, par):
         np.testing.assert_allclose(P.grad_h_at(b, x, y, idx), P.grad_h(b, x, y).ravel(), rtol=0, atol=1e-11)
         np.testing.assert_allclose(P.hess_h_vec_at(b, x, v, idx), P.hess_h_vec(b, x, v).ravel(), rtol=0,
                                    atol=1e-11)
+
+
+# ------------------------------------------------------------ BF16 operands
+def test_bf16_round_definition():
+    """Round to nearest, ties to even, at 8 significant bits (spacing 2^-7 on
+    [1, 2)): representable values stay, midpoints go to the even neighbour,
+    anything past a midpoint goes up; the input is first rounded to FP32."""
+    r = oracle.bf16_round
+    exact = np.array([0.0, 1.0, -3.5, 1 + 2.0 ** -7, 2.0 ** -126, 1.5 * 2.0 ** 100, -(1 + 127 * 2.0 ** -7)])
+    np.testing.assert_array_equal(r(exact), exact)
+    assert r(1 + 2.0 ** -8) == 1.0                          # tie, 1 is even
+    assert r(1 + 3 * 2.0 ** -8) == 1 + 2.0 ** -6            # tie, 1 + 2^-6 is even
+    assert r(-(1 + 2.0 ** -8)) == -1.0
+    assert r(1 + 2.0 ** -8 + 2.0 ** -20) == 1 + 2.0 ** -7   # past the tie
+    assert r(1 + 2.0 ** -8 - 2.0 ** -20) == 1.0
+    assert r(1 + 2.0 ** -8 + 2.0 ** -30) == 1.0             # FP32 first: the 2^-30 is gone
+    assert r(2 - 2.0 ** -9) == 2.0                          # carry into the exponent
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal(20000) * np.exp(rng.uniform(-20, 20, 20000))
+    q = r(v)
+    v32 = v.astype(np.float32).astype(np.float64)
+    assert np.all(np.abs(q - v32) <= 2.0 ** -8 * np.abs(v32))   # unit roundoff of 8 significant bits
+    assert np.all(np.diff(q[np.argsort(v32)]) >= 0)             # monotone
+    # the low 16 bits of every result are zero
+    assert np.all(q.astype(np.float32).view(np.uint32) & 0xFFFF == 0)
+
+
+def test_bf16_round_matches_torch_conversion():
+    """Special case that reduces to a library routine: PyTorch's CPU
+    float32 -> bfloat16 conversion also rounds to nearest even."""
+    import torch
+    rng = np.random.default_rng(4)
+    v = (rng.standard_normal(50000) * np.exp(rng.uniform(-30, 30, 50000))).astype(np.float32)
+    t = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(oracle.bf16_round(v), t)
