@@ -531,7 +531,7 @@ def run_ours(args):
         peak_tf = 1.25
     flops = passes * 2.0 * K * K * N
     achieved = flops / (kern_ms / 1e3) / 1e12
-    traffic = committed_traffic(ups)
+    traffic = committed_traffic("maid_run_rgb256_k15_traffic.json", MAID_SOURCES)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms_max / args.steps, "higher_is_better": True,
@@ -577,20 +577,28 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def committed_traffic(upper_iters):
-    """DRAM bytes per launch of the MAID kernel from the committed ncu summary,
-    or None when the kernel sources changed since it was taken."""
+MAID_SOURCES = ("adp.cu", "adp_device.cuh", "adp_engine.cuh", "adp_f32.cu", "adp_f32b.cu")
+TC_SOURCES = ("adp_tc.cu", "adp_tc.cuh", "adp_device.cuh")
+
+
+def sources_sha256(names):
+    """SHA-256 over the named files of the library's csrc/, in sorted order."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "maid_run_rgb256_k15_traffic.json")
-    try:
-        rec = json.load(open(path))
-    except Exception:
-        return None
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2502_09758_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in sorted(names):
         h.update(open(os.path.join(csrc, f), "rb").read())
-    if rec.get("sources_sha256") != h.hexdigest():
+    return h.hexdigest()
+
+
+def committed_traffic(name, sources):
+    """DRAM bytes per launch from the committed ncu summary profiles/<name>,
+    or None when the kernel's sources changed since it was taken."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", name)))
+    except Exception:
+        return None
+    if rec.get("sources_sha256") != sources_sha256(sources):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -666,6 +674,69 @@ def run_batch64(args):
     print(json.dumps(line), flush=True)
 
 
+def run_bf16_operator(args):
+    """B x with BF16 operands on the tensor cores against the FP32 operator
+    on the CUDA cores, on 3 x 2048 x 2048 with K = 31 (the largest kernel the
+    tensor-core operator takes) and on the 512^2 RGB K = 31 shape.  One JSON
+    line; value = useful TFLOP/s (2 K^2 per output) of the tensor-core
+    correlation at 2048^2.  Each timed launch follows an L2 flush; the
+    conversion kernels (FP32 image -> padded BF16, kernel -> Toeplitz bands)
+    are timed separately and reported beside it."""
+    import torch
+    from paper_2502_09758_gb300 import adp
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        peaks = json.load(f)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    clk = Clocks(str(getattr(torch.cuda.get_device_properties(0), "uuid", "")) or None)
+    res = {}
+    clk.start()
+    for name, (C, H, W, K) in (("rgb2048_k31", (3, 2048, 2048, 31)), ("rgb512_k31", (3, 512, 512, 31))):
+        g = torch.Generator(device="cpu").manual_seed(0)
+        y = torch.rand((C, H, W), generator=g).cuda()
+        b = (torch.rand((C, K, K), generator=g) / (K * K)).cuda()
+        prob = adp.Problem(adp.Params(C, H, W, K, prec=adp.ADP_F32), y, b)
+        x = torch.rand((C, H, W), generator=g).cuda()
+        o32, o16 = torch.empty_like(x), torch.empty_like(x)
+        t = {"fp32": [], "bf16": [], "prep": []}
+        for it in range(args.warmup + args.steps):
+            for kind in ("fp32", "bf16"):
+                flush.zero_()
+                if kind == "fp32":
+                    prob.apply_B(b, x, o32)
+                else:
+                    prob.apply_B_bf16(b, x, o16)
+                if it >= args.warmup:
+                    t[kind].append(prob.last_kernel_ms())
+                    if kind == "bf16":
+                        t["prep"].append(prob.bf16_prep_ms())
+        fl = 2.0 * K * K * C * H * W
+        m = {k: statistics.median(v) for k, v in t.items()}
+        res[name] = {"shape": [C, H, W, K], "fp32_ms": m["fp32"], "bf16_corr_ms": m["bf16"],
+                     "bf16_prep_ms": m["prep"], "fp32_tflops": fl / m["fp32"] / 1e9,
+                     "bf16_tflops_useful": fl / m["bf16"] / 1e9,
+                     "bf16_tflops_executed": fl * 64 / K / m["bf16"] / 1e9,
+                     "speedup_corr": m["fp32"] / m["bf16"], "speedup_with_prep": m["fp32"] / (m["bf16"] + m["prep"]),
+                     "rel_diff_vs_fp32": float((o16 - o32).norm() / o32.norm()),
+                     "bf16_grid": prob.bf16_grid_size()}
+        prob.close()
+        del prob
+        torch.cuda.empty_cache()
+    clocks = clk.stop()
+    big = res["rgb2048_k31"]
+    traffic = committed_traffic("tc_corr_rgb2048_k31_traffic.json", TC_SOURCES)
+    line = {"metric": "B x with BF16 operands and FP32 accumulation (tensor cores) vs FP32 (CUDA cores)",
+            "value": big["bf16_tflops_useful"], "unit": "TFLOP/s useful (2 K^2 flops per output)",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": big["bf16_corr_ms"],
+            "higher_is_better": True, "dtype": "bf16 operands, f32 accumulation", "data": "synthetic",
+            "config": {"workload": "rgb2048_k31_operator", "l2": "flushed (256 MB write) before each launch"},
+            "roofline": {"bound": "tensor", "achieved": big["bf16_tflops_useful"], "peak": peaks["bf16_tflops"],
+                         "unit": "TFLOP/s", "frac": big["bf16_tflops_useful"] / peaks["bf16_tflops"],
+                         "frac_executed": big["bf16_tflops_executed"] / peaks["bf16_tflops"],
+                         "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)", "traffic": traffic},
+            "gpu_launches": 3 * args.steps, "cases": res, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def run_profile_case(args):
     """A short fixed program for profiler captures: problem creation, then three
     lower-level launches of 4 FISTA iterations each (no timing, no JSON)."""
@@ -693,9 +764,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-torch-baseline", action="store_true",
                     help="skip the MAID written with PyTorch tensor ops (reported beside the run)")
-    ap.add_argument("--workload", default="rgb256_k15", choices=list(WORKLOAD_SPECS) + ["batch64"],
+    ap.add_argument("--workload", default="rgb256_k15",
+                    choices=list(WORKLOAD_SPECS) + ["batch64", "bf16_operator"],
                     help="rgb256_k15 (default) is the headline line; the others measure the other workloads: "
-                         "batch64 the 64-problem batch, batched vs one at a time")
+                         "batch64 the 64-problem batch, batched vs one at a time; bf16_operator the "
+                         "tensor-core operator against the FP32 one")
     ap.add_argument("--profile-case", default=None, choices=["rgb256_k15_motion", "rgb512_k31_gauss_perturbed",
                                                               "rgb2048_k63_motion_gauss"],
                     help="run a short fixed lower-level program for profiler captures")
@@ -705,6 +778,9 @@ def main():
         return
     if args.workload == "batch64":
         run_batch64(args)
+        return
+    if args.workload == "bf16_operator":
+        run_bf16_operator(args)
         return
     global EPS_STOP, MAX_UPPER, EPS0, STEP0
     spec = WORKLOAD_SPECS[args.workload]
