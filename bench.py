@@ -40,6 +40,12 @@ METRIC = "MAID time-to-tolerance (s) vs plain FP32 GPU; Mpixel·iter/s of fused 
 UNIT = "Mvalue·iter/s (values = C·H·W; iters = FISTA + CG iterations)"
 WORKLOAD = "rgb256_k15_motion"
 SM_COUNT, FP32_LANES = 152, 128
+# FFT path, bytes per value and convolution pass: row transforms read the
+# FP32 image and write complex values (4 + 8), the column phase reads the
+# complex image and the spectrum and writes the product's inverse (8 + 8 + 8),
+# the inverse rows read complex values and write the FP32 correlation (8 + 4),
+# the epilogue reads that correlation (4)
+FFT_BYTES_PER_VALUE = 52
 # MAID start for this workload (eps_0 = delta_0, alpha_0): the paper's 1e-2 / 0.1
 # are sized for its own scaling; these were picked by a grid search over
 # eps_0 in {1e-2, 1e-3, 1e-4} x alpha_0 in {1e-1, 1e-5, 1e-6, 1e-7} (every
@@ -438,6 +444,9 @@ def run_ours(args):
     a = torch.tensor(inst.a, dtype=tdt, device=dev)
     prob = adp.Problem(adp.Params(C, H, W, K, alpha=1e-2, reg_param=1e-2, beta=0.3,
                                   prec=adp.ADP_F64 if f64 else adp.ADP_F32), y, a)
+    fft = args.operator_path == "fft"
+    if fft:
+        prob.set_fft(True)
     batch = adp.Batch([prob])
     bufs = (torch.empty_like(a), torch.empty_like(y), torch.empty_like(y))
     for _ in range(args.warmup):
@@ -488,11 +497,16 @@ def run_ours(args):
         torch.cuda.synchronize()
         hs_ms.append((time.perf_counter() - t0) * 1e3)
 
-    # the plain host-driven GPU MAID on the same runs (two runs, the first warm)
-    plain_maid_run(prob, a, y)
-    pms, pups, pb, px = plain_maid_run(prob, a, y)
-    pxr = px.double().cpu().numpy()
-    plain_psnr = 10 * np.log10(1.0 / np.mean((pxr - inst.x_true) ** 2))
+    # the plain host-driven GPU MAID on the same runs (two runs, the first
+    # warm), with the direct correlation
+    pms, plain_psnr = None, None
+    if not args.no_plain:
+        prob.set_fft(False)
+        plain_maid_run(prob, a, y)
+        pms, pups, pb, px = plain_maid_run(prob, a, y)
+        pxr = px.double().cpu().numpy()
+        plain_psnr = 10 * np.log10(1.0 / np.mean((pxr - inst.x_true) ** 2))
+        prob.set_fft(fft)
 
     # the same method written with PyTorch tensor ops (one run, after a warm one)
     tms, tfused, tups, tb, tx = 0.0, 0, 0, None, None
@@ -531,19 +545,38 @@ def run_ours(args):
         peak_tf = 1.25
     flops = passes * 2.0 * K * K * N
     achieved = flops / (kern_ms / 1e3) / 1e12
-    traffic = committed_traffic("maid_run_rgb256_k15_traffic.json", MAID_SOURCES)
+    traffic = committed_traffic("maid_run_rgb256_k15_traffic.json", MAID_SOURCES) if not fft else None
+    if fft:   # FFT path: bound by memory traffic, FFT_BYTES_PER_VALUE per value and pass
+        hbm = float(pk.get("hbm_gbs", 6787.2))
+        ach_gbs = passes * FFT_BYTES_PER_VALUE * N / (kern_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm, "unit": "GB/s", "frac": ach_gbs / hbm,
+                "traffic": traffic, "kernel": "adp_kernel<float, FFT> (persistent MAID step, graph-replayed)",
+                "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "bytes_basis": f"{FFT_BYTES_PER_VALUE} B per value and convolution pass (the FFT pass's "
+                               "row, column and inverse-row phases and its epilogue read), passes counted "
+                               "on the device",
+                "direct_equivalent_tflops": achieved}
+    else:
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved / peak_tf, "traffic": traffic,
+                "kernel": "adp_kernel<float> (persistent MAID step, graph-replayed)",
+                "peak_basis": ("nominal GB300 FP64 rate" if f64 else
+                               f"152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"),
+                "flops_basis": "2 K^2 C H W per convolution pass, passes counted on the device"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": spec["dtype"], "data": "synthetic",
-        "config": {"workload": spec["name"], "C": C, "H": H, "W": W, "K": K, "alpha": 1e-2, "huber": 1e-2,
+        "config": {"workload": spec["name"] + ("_fft" if fft else ""), "C": C, "H": H, "W": W, "K": K, "alpha": 1e-2, "huber": 1e-2,
                    "beta": 0.3, "maid_eps0": EPS0, "maid_step0": STEP0, "eps_stop": EPS_STOP,
                    "max_upper": MAX_UPPER, "step": "one MAID run to the stop rule",
                    "l2": "flushed between timed runs (256 MB write)", "parallelism": f"replicas x{world}"},
         "maid": {"time_to_tolerance_s": tot_ms_max / args.steps / 1e3,
                  "form": "device-resident run: one cooperative launch runs all upper iterations (a CUDA graph of one kernel node)",
                  "host_stepped_s": statistics.median(hs_ms) / 1e3,
-                 "plain_gpu_maid_s": pms / 1e3, "speedup_vs_plain": pms / (tot_ms_max / args.steps),
+                 "operator_path": "fft" if fft else "direct",
+                 "plain_gpu_maid_s": pms / 1e3 if pms else None,
+                 "speedup_vs_plain": pms / (tot_ms_max / args.steps) if pms else None,
                  "torch_maid_s": (tms / 1e3) if tms else None,
                  "torch_maid_fused_iters": tfused or None, "torch_maid_upper_iters": tups or None,
                  "torch_final_psnr_x_db": torch_psnr if tms else None,
@@ -553,12 +586,7 @@ def run_ours(args):
                  "final_psnr_x_db": psnr_x, "final_psnr_b_db": psnr_b, "plain_final_psnr_x_db": plain_psnr,
                  "grid_ctas": prob.grid_size(), "warps_per_cta": prob.warps_per_cta(),
                  "graph_device_ms_per_run": kern_ms / args.steps},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tf, "traffic": traffic,
-                     "kernel": "adp_kernel<float> (persistent MAID step, graph-replayed)",
-                     "peak_basis": ("nominal GB300 FP64 rate" if f64 else
-                                    f"152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"),
-                     "flops_basis": "2 K^2 C H W per convolution pass, passes counted on the device"},
+        "roofline": roof,
         "e2e": {"value": e2e_units / (e2e_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,            # one cooperative launch per MAID run
@@ -747,6 +775,8 @@ def run_profile_case(args):
     y = torch.tensor(inst.y, dtype=torch.float32, device="cuda")
     a = torch.tensor(inst.a, dtype=torch.float32, device="cuda")
     prob = adp.Problem(adp.Params(C, H, W, inst.K, alpha=1e-2, reg_param=1e-2, beta=0.3), y, a)
+    if args.operator_path == "fft":
+        prob.set_fft(True)
     for _ in range(3):
         x = y.clone()
         prob.lower_solve(a, x, 0.0, 4)
@@ -762,6 +792,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--operator-path", default="direct", choices=["direct", "fft"],
+                    help="fft: the MAID runs evaluate B, B^T and A through 2-D FFTs (adp_set_fft)")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the plain host-driven GPU MAID (reported beside the run)")
     ap.add_argument("--no-torch-baseline", action="store_true",
                     help="skip the MAID written with PyTorch tensor ops (reported beside the run)")
     ap.add_argument("--workload", default="rgb256_k15",

@@ -27,6 +27,7 @@ ADP_REG_HUBER_TV, ADP_REG_SQRT_TV, ADP_REG_QUAD = 0, 1, 2
 # every entry point declared in include/adp.h
 EXPORTS = ("adp_problem_create", "adp_problem_destroy", "adp_apply_B", "adp_apply_Bt",
            "adp_apply_B_bf16", "adp_apply_Bt_bf16", "adp_bf16_prep_ms_last", "adp_bf16_grid_size",
+           "adp_set_fft", "adp_fft_enabled",
            "adp_grad_lower", "adp_hess_vec", "adp_lower_solve", "adp_upper_loss", "adp_hypergrad",
            "adp_cross_t", "adp_maid_init", "adp_maid_step", "adp_conv_passes_last",
            "adp_grid_size", "adp_warps_per_cta", "adp_last_kernel_ms", "adp_trace_enable",
@@ -84,6 +85,8 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
             "adp_apply_Bt_bf16": (i, [P, vp, vp, vp]),
             "adp_bf16_prep_ms_last": (ct.c_double, [P]),
             "adp_bf16_grid_size": (i, [P]),
+            "adp_set_fft": (i, [P, i]),
+            "adp_fft_enabled": (i, [P]),
             "adp_grad_lower": (i, [P, vp, vp, vp, dp]),
             "adp_hess_vec": (i, [P, vp, vp, vp, vp]),
             "adp_lower_solve": (i, [P, vp, vp, d, i, ip, dp]),
@@ -238,6 +241,13 @@ class Problem:
         out = self._new_img() if out is None else out
         _check(self.lib.adp_apply_Bt_bf16(self.handle, self._k(b, "b"), self._i(z, "z"), self._i(out, "out")))
         return out
+
+    def set_fft(self, enable=True):
+        """Evaluate the operators of later calls through 2-D FFTs (FP32, power-of-two H, W)."""
+        _check(self.lib.adp_set_fft(self.handle, 1 if enable else 0))
+
+    def fft_enabled(self) -> bool:
+        return bool(self.lib.adp_fft_enabled(self.handle))
 
     def bf16_prep_ms(self) -> float:
         return float(self.lib.adp_bf16_prep_ms_last(self.handle))

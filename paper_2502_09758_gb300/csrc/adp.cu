@@ -30,6 +30,7 @@ namespace adp {
 const void *kernel_f32();
 const void *kernel_f64();
 const void *kernel_f32_batched();
+const void *kernel_f32_fft();
 const void *kernel_f64_batched();
 } // namespace adp
 
@@ -85,6 +86,10 @@ struct adp_problem {
     float last_ms;
     TcPlan *tc;            // BF16 tensor-core operator workspace (made on first use)
     TcTimes tc_times;
+    // FFT operator path (adp_set_fft): on/off, log2 sizes, column block, buffers
+    int fft, flogH, flogW, fcb, frb;
+    float2 *fz, *fs, *ftw;  // complex scratch image, kernel spectrum, twiddles (H/2 then W/2)
+    float *fout, *fc;       // correlation of the last FFT pass; B^T y of the current lower solve
 };
 
 // ------------------------------------------------------------ tensor maps
@@ -180,6 +185,11 @@ static Ctx<T> make_ctx(const adp_problem *p)
     c.part = p->part; c.zpart = p->zpart; c.bar = p->bar; c.out = p->dout;
     const double to = q.wait_timeout_s > 0 ? q.wait_timeout_s : 2.0;
     c.timeout_ns = (long long)(to * 1e9);
+    if (p->fft) {
+        c.fft = 1; c.flogH = p->flogH; c.flogW = p->flogW; c.fcb = p->fcb; c.frb = p->frb;
+        c.fz = p->fz; c.fs = p->fs; c.fout = (T *)p->fout; c.fc = (T *)p->fc;
+        c.ftwH = p->ftw; c.ftwW = p->ftw + q.H / 2;
+    }
     return c;
 }
 
@@ -191,7 +201,7 @@ static adp_status launch(adp_problem *p, Job<T> &jb)
     CK(cudaMemsetAsync(p->bar, 0, sizeof(unsigned), p->stream));
     CK(cudaMemsetAsync(p->dout, 0, sizeof(DevOut), p->stream));
     void *args[] = {(void *)&cx, (void *)&jb};
-    const void *fn = std::is_same<T, float>::value ? kernel_f32() : kernel_f64();
+    const void *fn = std::is_same<T, float>::value ? (p->fft ? kernel_f32_fft() : kernel_f32()) : kernel_f64();
     CK(cudaEventRecord(p->ev0, p->stream));
     CK(cudaLaunchCooperativeKernel(fn, dim3(p->grid), dim3(32 * p->nw), args, p->smem, p->stream));
     CK(cudaEventRecord(p->ev1, p->stream));
@@ -256,6 +266,8 @@ void adp_problem_destroy(adp_problem *p)
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
     tc_plan_destroy(p->tc);
+    void *fptrs[] = {p->fz, p->fs, p->ftw, p->fout, p->fc};
+    for (void *q : fptrs) if (q) cudaFree(q);
     free(p->a_host);
     free(p);
 }
@@ -445,6 +457,78 @@ adp_status adp_apply_Bt_bf16(adp_problem *p, const void *b, const void *z, void 
 {
     return apply_bf16(p, b, z, out, true);
 }
+
+static int log2_exact(int n)
+{
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return (1 << l) == n ? l : -1;
+}
+
+adp_status adp_set_fft(adp_problem *p, int enable)
+{
+    if (!p) return set_err(ADP_EINVAL, "null problem%s", "", 0);
+    if (!enable) {
+        p->fft = 0;
+        return ADP_OK;
+    }
+    const adp_params &q = p->prm;
+    if (q.prec != ADP_F32) return set_err(ADP_EINVAL, "FFT path needs an ADP_F32 problem%s", "", 0);
+    const int lh = log2_exact(q.H), lw = log2_exact(q.W);
+    if (lh < 1 || lw < 1 || q.H > 8192 || q.W > 8192)
+        return set_err(ADP_EINVAL, "FFT path needs H and W powers of two in 2..8192%s", "", 0);
+    // shared scratch of the FFT phases: the warp regions of a CTA
+    const size_t esz = sizeof(float);
+    const Layout<float> L(q.C, q.K, p->nw, p->g.wsm);
+    const size_t scratch = (size_t)p->nw * L.warp_elems * esz;
+    if ((size_t)q.W * 8 > scratch)
+        return set_err(ADP_EINVAL, "FFT path: image rows too long for shared memory%s (W = %lld)", "", q.W);
+    // columns per column block and rows per row batch: powers of two, at most
+    // 32, within the scratch, and small enough that every CTA gets a block
+    auto pick = [&](int len, int count_total, int limit) {
+        int v = 32;
+        while (v > 1 && ((size_t)len * v * 8 > scratch || v > limit || (long long)count_total / v < p->grid)) v >>= 1;
+        return v;
+    };
+    const int cb = pick(q.H, q.C * q.W, q.W), rb = pick(q.W, q.C * q.H, q.H);
+    if ((size_t)q.H * cb * 8 > scratch)
+        return set_err(ADP_EINVAL, "FFT path: image columns too long for shared memory%s (H = %lld)", "", q.H);
+    CK(cudaSetDevice(p->device));
+    {   // the FFT instantiation must be co-resident at the problem's grid
+        int nsm = 0, maxsmem = 0, occ = 0;
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
+        CK(cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+        CK(optin_dynamic_smem(kernel_f32_fft(), maxsmem));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel_f32_fft(), 32 * p->nw, p->smem));
+        if ((long long)occ * nsm < p->grid)
+            return set_err(ADP_EINVAL, "FFT path: kernel not co-resident at the problem's grid%s (%lld CTAs)", "",
+                           p->grid);
+    }
+    if (!p->fz) {
+        const size_t n = (size_t)q.C * q.H * q.W;
+        CK(cudaMalloc((void **)&p->fz, n * sizeof(float2)));
+        CK(cudaMalloc((void **)&p->fs, n * sizeof(float2)));
+        CK(cudaMalloc((void **)&p->fout, n * sizeof(float)));
+        CK(cudaMalloc((void **)&p->fc, n * sizeof(float)));
+        CK(cudaMalloc((void **)&p->ftw, (size_t)(q.H / 2 + q.W / 2) * sizeof(float2)));
+        // twiddles exp(-2 pi i j / n), j < n/2, computed in double and rounded once
+        std::vector<float2> tw((size_t)(q.H / 2 + q.W / 2));
+        const double pi = 3.14159265358979323846;
+        for (int j = 0; j < q.H / 2; ++j)
+            tw[j] = make_float2((float)cos(2 * pi * j / q.H), (float)-sin(2 * pi * j / q.H));
+        for (int j = 0; j < q.W / 2; ++j)
+            tw[q.H / 2 + j] = make_float2((float)cos(2 * pi * j / q.W), (float)-sin(2 * pi * j / q.W));
+        CK(cudaMemcpy(p->ftw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    }
+    p->flogH = lh;
+    p->flogW = lw;
+    p->fcb = cb;
+    p->frb = rb;
+    p->fft = 1;
+    return ADP_OK;
+}
+
+int adp_fft_enabled(adp_problem *p) { return p ? p->fft : 0; }
 
 double adp_bf16_prep_ms_last(adp_problem *p) { return p && p->tc ? (double)p->tc_times.prep_ms : -1.0; }
 int adp_bf16_grid_size(adp_problem *p) { return p ? tc_grid(p->tc) : 0; }
@@ -674,6 +758,9 @@ static void batch_fill(adp_batch *bt, const adp_maid_state *st, void *const *b, 
         c.out = bt->dout + i;
         c.totals = resident ? bt->dtot + i : nullptr;
         c.trace = nullptr;
+        // a batch of several problems runs the direct operator (the FFT scratch
+        // is sized for a problem's own launch shape, which only a batch of one keeps)
+        if (bt->n > 1) c.fft = 0;
         c.trace_cap = 0;
         memcpy(bt->hctx + i * bt->ctx_bytes, &c, sizeof c);
         Job<T> j;
@@ -755,7 +842,7 @@ static void batch_rebalance(adp_batch *bt)
 static adp_status batch_launch(adp_batch *bt, cudaStream_t stream)
 {
     const bool one = bt->n == 1;
-    const void *fn = one ? (bt->prec == ADP_F32 ? kernel_f32() : kernel_f64())
+    const void *fn = one ? (bt->prec == ADP_F32 ? (bt->ps[0]->fft ? kernel_f32_fft() : kernel_f32()) : kernel_f64())
                          : (bt->prec == ADP_F32 ? kernel_f32_batched() : kernel_f64_batched());
     void *ctxp = bt->dctx, *jobp = bt->djob;
     int *fp = bt->dfirst;

@@ -540,6 +540,12 @@ struct Ctx {
     DevOut *out;
     MaidTotals *totals;                // optional running totals (device-resident runs)
     long long timeout_ns;
+    // FFT operator path (FP32 problems with power-of-two H and W; fft = 0: direct)
+    int fft, flogH, flogW, fcb, frb;   // log2 H, log2 W, columns per column block, rows per row batch
+    float2 *fz, *fs;                   // complex scratch image and kernel spectrum, C x H x W each
+    T *fout;                           // the correlation of the last FFT pass, dense C x H x W
+    T *fc;                             // B^T y_delta of the current lower solve (FFT path), dense
+    const float2 *ftwH, *ftwW;         // twiddles exp(-2 pi i j / n), j < n/2, for n = H and n = W
 };
 
 template <typename T>

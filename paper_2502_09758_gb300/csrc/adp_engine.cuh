@@ -32,6 +32,9 @@
 #pragma once
 
 #include "adp_device.cuh"
+#include "adp_fft.cuh"
+
+#include <type_traits>
 
 namespace adp {
 
@@ -44,6 +47,9 @@ __shared__ double g_redd[MAXNW];
 __shared__ __align__(16) double g_tau[MAXC];
 __shared__ __align__(16) double g_gbuf[GT_MAX];
 __shared__ int g_sflag;
+// each warp's two mbarriers (outside the warp regions, which the FFT phases
+// reuse as one CTA-wide scratch area between passes)
+__shared__ __align__(8) uint64_t g_mbar[MAXNW][2];
 
 // Report of a MAID step, accumulated by thread 0 of each CTA (shared memory,
 // so that it occupies no registers while the solves run).
@@ -54,7 +60,9 @@ struct MaidRep {
 };
 __shared__ MaidRep g_rep;
 
-template <typename T>
+// FFTP: compile the FFT operator path in (a separate instantiation, so that
+// the direct program's register allocation does not carry it).
+template <typename T, bool FFTP = false>
 struct Eng {
     using Sc = Scal<T>;
     using S = typename Sc::S;      // reduction / control scalar (float-float or double)
@@ -62,6 +70,7 @@ struct Eng {
     static constexpr int PC = Cfg<T>::PC;
     static constexpr int NX = PC + MR - 1;
     static constexpr int EWB = 4;  // element-wise phases: loads issued per batch per thread
+    static constexpr bool kFFT = FFTP && std::is_same<T, float>::value;   // FFT path: FP32 only
     const Ctx<T> &cx;
     const Ctx<T> *mc;              // where the tensor maps live (parameter or global space)
     const T *wF, *wT;              // kernel orientations in use (shared memory or a global slot)
@@ -85,7 +94,10 @@ struct Eng {
     __device__ T *t1() const { return sb0 + 2 * stage_elems(); }
     __device__ T *t2() const { return t1() + TILE1; }
     __device__ T *tF() const { return t2() + TILE1; }
-    __device__ uint64_t *mbar() const { return reinterpret_cast<uint64_t *>(tF() + TILEI); }
+    __device__ uint64_t *mbar() const { return g_mbar[warp]; }
+    __device__ int warp_elems() const { return 2 * stage_elems() + 2 * TILE1 + TILEI + 32; }
+    // the warp regions of the CTA, contiguous: complex scratch of the FFT phases
+    __device__ float2 *fft_scratch() const { return reinterpret_cast<float2 *>(sb0 - warp * warp_elems()); }
     __device__ S *red() const { return reinterpret_cast<S *>(g_red); }
     __device__ S *bcast() const { return reinterpret_cast<S *>(g_bcast); }
     __device__ S *gbuf() const { return reinterpret_cast<S *>(g_gbuf); }
@@ -269,6 +281,9 @@ struct Eng {
         wT = Tt;
         if (cx.wsm) __syncthreads();
         else sync();
+        if constexpr (kFFT) {
+            if (cx.fft) spectrum(b);
+        }
     }
 
     __device__ S *partS(int slot) const { return reinterpret_cast<S *>(cx.part) + slot * nblk; }
@@ -298,6 +313,202 @@ struct Eng {
         corr_on(s, flip, c, p0, 0, cx.K, acc);
     }
 
+    // ------------------------------------------------------------ FFT path
+    // Row transforms of batches of cx.frb consecutive image rows (the C*H
+    // rows, channel-major) and column transforms of blocks of cx.fcb columns,
+    // in the CTA's scratch (the warp regions).  Frequencies are kept in
+    // bit-reversed order along both axes (forward DIF, inverse DIT), in cx.fz
+    // and in the spectrum cx.fs alike.  Copies between global memory and the
+    // scratch go through registers FU elements per thread at a time, so that
+    // a thread has that many global loads in flight (the scratch is reached
+    // through a generic pointer, so loads would otherwise wait for the
+    // preceding stores).
+    static constexpr int FU = 8;
+    enum { FM_B = 0, FM_BT = 1, FM_GRAM = 2 };   // what multiplies the image's spectrum
+
+    // for e = tid, tid + blockDim, ... < n: v = ld(e), then st(e, v), FU at a
+    // time (the loads past n re-read element n - 1 and are discarded)
+    template <typename Ld, typename St>
+    __device__ void fft_copy(int n, Ld ld, St st)
+    {
+        const int bd = blockDim.x;
+        for (int e0 = tid(); e0 < n; e0 += FU * bd) {
+            float2 v[FU];
+#pragma unroll
+            for (int u = 0; u < FU; ++u) v[u] = ld(min(e0 + u * bd, n - 1));
+#pragma unroll
+            for (int u = 0; u < FU; ++u)
+                if (e0 + u * bd < n) st(e0 + u * bd, v[u]);
+        }
+    }
+
+    // forward row transforms of rows r0 .. r0+frb-1 of val(c, i, j) into cx.fz
+    template <typename Val>
+    __device__ void fft_rows_fwd(int r0, Val val)
+    {
+        float2 *a = fft_scratch();
+        const int lh = cx.flogH, W = cx.W, lw = cx.flogW, RB = cx.frb;
+        fft_copy(RB * W,
+                 [=](int e) {
+                     const int ri = r0 + (e >> lw);
+                     return make_float2(val(ri >> lh, ri & ((1 << lh) - 1), e & (W - 1)), 0.f);
+                 },
+                 [=](int e, float2 v) { a[fslot(e >> lw, e & (W - 1), RB)] = v; });
+        __syncthreads();
+        fft_stages<true>(a, W, lw, RB, cx.ftwW, false);
+        float2 *z = cx.fz + (long long)r0 * W;
+        fft_copy(RB * W, [=](int e) { return a[fslot(e >> lw, e & (W - 1), RB)]; },
+                 [=](int e, float2 v) { z[e] = v; });
+        __syncthreads();
+    }
+
+    // Kernel spectrum F(k) of kernel bk (C x K x K) into cx.fs: the kernel
+    // image k(u, v) = bk[u + r, v + r] at (u mod H, v mod W) (taps that wrap
+    // onto the same pixel add up), then the 2-D forward transform.
+    __device__ bool spectrum(const T *bk)
+    {
+        if constexpr (kFFT) {
+            if (!sync()) return false;            // no CTA still reads the scratch image
+            const int H = cx.H, W = cx.W, K = cx.K, r = cx.r;
+            for (int r0 = bid * cx.frb; r0 < cx.C * H; r0 += nblk * cx.frb)
+                fft_rows_fwd(r0, [=](int c, int i, int j) {
+                    const T *bc = bk + (long long)c * K * K;
+                    float v = 0.f;
+                    // kernel rows and columns landing on (i, j): p = i + r (mod H), q = j + r (mod W)
+                    for (int pp = (i + r) % H; pp < K; pp += H)
+                        for (int qq = (j + r) % W; qq < K; qq += W) v += __ldcg(bc + pp * K + qq);
+                    return v;
+                });
+            if (!sync()) return false;
+            fft_columns(FM_B, true);
+            return sync();
+        } else {
+            return false;
+        }
+    }
+
+    // Column transforms over cx.fz in blocks of cx.fcb columns: forward, then
+    // times the spectrum (FM_B), its conjugate (FM_BT) or its squared modulus
+    // (FM_GRAM, the operator B^T B), and inverse back into cx.fz; or
+    // (spec_only) the forward transform alone into cx.fs.
+    __device__ void fft_columns(int fm, bool spec_only)
+    {
+        float2 *a = fft_scratch();
+        const int H = cx.H, W = cx.W, lh = cx.flogH, CB = cx.fcb, lcb = __ffs(CB) - 1, nbc = W / CB;
+        for (int cbi = bid; cbi < cx.C * nbc; cbi += nblk) {
+            const int c = cbi / nbc, j0 = (cbi - c * nbc) * CB;
+            const long long o = (long long)c * H * W + j0;
+            auto gidx = [=](int e) { return (long long)(e >> lcb) * W + (e & (CB - 1)); };
+            auto sidx = [=](int e) { return fslot(e & (CB - 1), e >> lcb, CB); };
+            const float2 *zc = cx.fz + o;
+            fft_copy(H * CB, [=](int e) { return __ldcg(zc + gidx(e)); }, [=](int e, float2 v) { a[sidx(e)] = v; });
+            __syncthreads();
+            fft_stages<true>(a, H, lh, CB, cx.ftwH, false);
+            if (spec_only) {
+                float2 *sc = cx.fs + o;
+                fft_copy(H * CB, [=](int e) { return a[sidx(e)]; }, [=](int e, float2 v) { sc[gidx(e)] = v; });
+                __syncthreads();
+                continue;
+            }
+            const float2 *sc = cx.fs + o;
+            const float sgn = fm == FM_B ? 1.f : -1.f;
+            fft_copy(H * CB, [=](int e) { return __ldcg(sc + gidx(e)); },
+                     [=](int e, float2 sp) {
+                         const int sl = sidx(e);
+                         if (fm == FM_GRAM) {
+                             const float m2 = fmaf(sp.x, sp.x, sp.y * sp.y);
+                             a[sl] = make_float2(a[sl].x * m2, a[sl].y * m2);
+                         } else {
+                             a[sl] = cmul(a[sl], make_float2(sp.x, sgn * sp.y));
+                         }
+                     });
+            __syncthreads();
+            fft_stages<false>(a, H, lh, CB, cx.ftwH, true);
+            float2 *zw = cx.fz + o;
+            fft_copy(H * CB, [=](int e) { return a[sidx(e)]; }, [=](int e, float2 v) { zw[gidx(e)] = v; });
+            __syncthreads();
+        }
+    }
+
+    // B img (FM_B), B^T img (FM_BT) or B^T B img (FM_GRAM) for buffer img
+    // through the 2-D transform with the spectrum of the loaded kernel, into
+    // dst (dense; cx.fout when null); ends with a grid barrier.
+    __device__ bool fft_conv(int fm, int img, T *dst = nullptr)
+    {
+        if constexpr (kFFT) {
+            float2 *a = fft_scratch();
+            const int H = cx.H, W = cx.W, lw = cx.flogW, RB = cx.frb;
+            const T *src = buf(img);
+            const long long HWp = cx.HWp;
+            const int Wp = cx.Wp, Gy = cx.Gy, Gx = cx.Gx;
+            for (int r0 = bid * RB; r0 < cx.C * H; r0 += nblk * RB)
+                fft_rows_fwd(r0, [=](int c, int i, int j) {
+                    return (float)__ldcg(src + c * HWp + (long long)(i + Gy) * Wp + Gx + j);
+                });
+            if (!sync()) return false;
+            fft_columns(fm, false);
+            if (!sync()) return false;
+            T *out = dst ? dst : cx.fout;
+            const float scale = 1.f / ((float)H * (float)W);
+            for (int r0 = bid * RB; r0 < cx.C * H; r0 += nblk * RB) {
+                const float2 *z = cx.fz + (long long)r0 * W;
+                fft_copy(RB * W, [=](int e) { return __ldcg(z + e); },
+                         [=](int e, float2 v) { a[fslot(e >> lw, e & (W - 1), RB)] = v; });
+                __syncthreads();
+                fft_stages<false>(a, W, lw, RB, cx.ftwW, true);
+                T *o = out + (long long)r0 * W;
+                fft_copy(RB * W, [=](int e) { return a[fslot(e >> lw, e & (W - 1), RB)]; },
+                         [=](int e, float2 v) { o[e] = v.x * scale; });
+                __syncthreads();
+            }
+            return sync();
+        } else {
+            return false;
+        }
+    }
+
+    // pass() on the FFT path: the correlation comes from fft_conv, then the
+    // strips run the same epilogue with the same staged operands.
+    template <typename Epi>
+    __device__ S pass_fft(int fm, int img0, int t1b, int t2b, int fb, Epi epi)
+    {
+        S part = Sc::zero();
+        if (!fft_conv(fm, img0)) return part;
+        const unsigned eb = (t1b >= 0 ? bytes_1() : 0u) + (t2b >= 0 ? bytes_1() : 0u) + (fb >= 0 ? bytes_i() : 0u);
+        for (int s = gw(); s < cx.nstrips; s += TW()) {
+            int c, row0, col0;
+            strip_of(s, c, row0, col0);
+            if (eb) {
+                if (lane == 0) {
+                    uint64_t *mb = &mbar()[0];
+                    mbar_expect_tx(mb, eb);
+                    if (t1b >= 0) box_1(t1(), t1b, c, row0, col0, mb);
+                    if (t2b >= 0) box_1(t2(), t2b, c, row0, col0, mb);
+                    if (fb >= 0) box_i(tF(), fb, c, row0, col0, mb);
+                }
+                if (!land(0)) return part;
+            }
+            T sum = T(0);
+            const int gj = col0 + lane;
+            const long long cbase = (long long)c * cx.HW;
+            T acc[MR];                     // all loads in flight before the epilogue's stores
+#pragma unroll
+            for (int m = 0; m < MR; ++m) {
+                const int gi = row0 + m;
+                acc[m] = (gi < cx.H && gj < cx.W) ? __ldcg(cx.fout + cbase + (long long)gi * cx.W + gj) : T(0);
+            }
+#pragma unroll
+            for (int m = 0; m < MR; ++m) {
+                const int gi = row0 + m;
+                if (gi < cx.H && gj < cx.W)
+                    sum += epi(c, gi, gj, cbase + (long long)gi * cx.W + gj, m, acc[m], tF()[m * 32 + lane]);
+            }
+            part = Sc::addv(part, sum);
+            __syncwarp();                  // epilogue reads before the next strip's copies
+        }
+        return part;
+    }
+
     // One convolution pass over all strips.  img0 is staged in stages of NX
     // rows (double-buffered).  With img1 >= 0 each stage holds img0 in sb0 and
     // img1 in sb1() (single-buffered) and prep(stage, c, row0, col0) combines them
@@ -309,6 +520,9 @@ struct Eng {
     template <typename Prep, typename Epi>
     __device__ S pass(bool flip, int img0, int img1, int t1b, int t2b, int fb, Prep prep, Epi epi)
     {
+        if constexpr (kFFT) {
+            if (cx.fft) return pass_fft(flip ? FM_B : FM_BT, img0, t1b, t2b, fb, epi);   // img1 is never set here
+        }
         S part = Sc::zero();
         if (!alive || tmafail) return part;
         if (lane == 0) fence_proxy_async();
@@ -482,10 +696,12 @@ struct Eng {
     // Returns this warp's share of <v, out>.  Weights of b loaded.
     __device__ S hess_vec(int bx, int bv, int bo, T *dense_out)
     {
-        T *U = buf(B_U);
-        pass(true, bv, -1, -1, -1, -1, noprep,
-             [=](int c, int gi, int gj, long long, int, T val, T) { put(U, c, gi, gj, val); return T(0); });
-        if (!sync()) return Sc::zero();
+        if (!gram()) {
+            T *U = buf(B_U);
+            pass(true, bv, -1, -1, -1, -1, noprep,
+                 [=](int c, int gi, int gj, long long, int, T val, T) { put(U, c, gi, gj, val); return T(0); });
+            if (!sync()) return Sc::zero();
+        }
         return hess_vec_b(bx, bv, bo, dense_out);
     }
 
@@ -495,12 +711,22 @@ struct Eng {
     {
         const T al = cx.alphaT;
         T *O = buf(bo);
-        return pass(false, B_U, -1, bx, bv, -1, noprep, [=](int c, int gi, int gj, long long g, int m, T v, T) {
+        auto epi = [=](int c, int gi, int gj, long long g, int m, T v, T) {
             const T hv = v + al * tv_hess(t1(), t2(), m);
             if (dense_out) dense_out[g] = hv;
             else put(O, c, gi, gj, hv);
             return hv * center1(t2(), m);
-        });
+        };
+        if (gram()) return pass_fft(FM_GRAM, bv, bx, bv, -1, epi);   // B^T B v in one transform pair
+        return pass(false, B_U, -1, bx, bv, -1, noprep, epi);
+    }
+
+    // FFT path: B^T B applied through |F(k)|^2 in one forward/inverse pair
+    // (the FISTA gradient and the Hessian products)
+    __device__ bool gram() const
+    {
+        if constexpr (kFFT) return cx.fft != 0;
+        else return false;
     }
 
     // 1/L_c for FISTA on channel c with kernel b: L_c = ||b_c||_1^2 + 8 alpha sup phi''
@@ -540,6 +766,9 @@ struct Eng {
         compute_tau(b);
         copy_buf(B_X0, B_Y0, bin);
         if (!sync()) return 0;
+        // FFT path: grad = B^T B y - B^T y_delta + alpha grad J(y), with B^T y_delta once
+        if (gram() && !fft_conv(FM_BT, B_Y, cx.fc)) return 0;
+        const T *FC = cx.fc;
         int xp = B_X0, xn = B_X1, yc = B_Y0, yn = B_Y1;
         const T al = cx.alphaT;
         const T *tauc = tau();
@@ -555,8 +784,8 @@ struct Eng {
         for (;; ++k) {
             const int ycur = yc;
             if (pending && warp == 0) grid_issue<T>(partS((k - 1) & 1), nblk, gbuf());
-            // phase A: U = B y_k - y
-            residual(ycur, B_U);
+            // phase A: U = B y_k - y (not on the FFT path)
+            if (!gram()) residual(ycur, B_U);
             if (pending) {
                 if (warp == 0) {
                     const S s = grid_finish<T>(nblk, gbuf());
@@ -582,14 +811,18 @@ struct Eng {
             // y_{k+1} = x_{k+1} + theta_{k+1} (x_{k+1} - x_k); ||G||^2
             T *XN = buf(xn), *YN = buf(yn);
             const T th = thn;
-            const S part = pass(false, B_U, -1, ycur, -1, xp, noprep,
-                                [=](int c, int gi, int gj, long long, int m, T v, T xpv) {
-                                    const T gr = v + al * tv_grad(t1(), m);
-                                    const T xnv = center1(t1(), m) - tauc[c] * gr;
-                                    XN[pidx(c, gi, gj)] = xnv;     // read back only as an interior operand
-                                    put(YN, c, gi, gj, xnv + th * (xnv - xpv));
-                                    return gr * gr;
-                                });
+            auto epiB = [=](int c, int gi, int gj, long long, int m, T v, T xpv) {
+                const T gr = v + al * tv_grad(t1(), m);
+                const T xnv = center1(t1(), m) - tauc[c] * gr;
+                XN[pidx(c, gi, gj)] = xnv;     // read back only as an interior operand
+                put(YN, c, gi, gj, xnv + th * (xnv - xpv));
+                return gr * gr;
+            };
+            const S part = gram() ? pass_fft(FM_GRAM, ycur, ycur, -1, xp,
+                                             [=](int c, int gi, int gj, long long g, int m, T v, T xpv) {
+                                                 return epiB(c, gi, gj, g, m, v - __ldcg(FC + g), xpv);
+                                             })
+                                  : pass(false, B_U, -1, ycur, -1, xp, noprep, epiB);
             const S cta = block_sum<T>(part, red());
             if (tid() == 0) partS(k & 1)[bid] = cta;
             // momentum of the next iteration, before waiting on the barrier
@@ -597,7 +830,7 @@ struct Eng {
             const S tn_next = next_t(t_next);
             const T thn_next = (T)Sc::to_elem(Sc::div(Sc::addv(t_next, -1), tn_next));
             if (!sync()) return k;
-            passes += 2;
+            passes += gram() ? 1 : 2;
             if (k >= max_iters) {          // cap: the norm of y_k is needed now
                 const S ss = grid_total<T>(partS(k & 1), nblk, gbuf(), bcast());
                 if (!Sc::finite(ss)) {
@@ -702,7 +935,7 @@ struct Eng {
         if (!zero_start) {
             hess_vec(bx, B_Q, B_HP, nullptr);
             if (!sync()) return 0;
-            passes += 2;
+            passes += gram() ? 1 : 2;
         }
         auto interior = [&](int row, int j) {
             const int pi = row % cx.Hp;
@@ -763,13 +996,21 @@ struct Eng {
                 }
             };
             auto epiU = [=](int c, int gi, int gj, long long, int, T v, T) { put(U, c, gi, gj, v); return T(0); };
-            if (first) pass(true, pc, -1, -1, -1, -1, noprep, epiU);
-            else pass(true, B_R, po, -1, -1, -1, combine, epiU);
+            if (gram()) {              // p = r + beta p over the whole padded buffer (B p is not needed)
+                if (!first) {
+                    const T *Rr = buf(B_R), *Po = buf(po);
+                    for (long long e = gstart(); e < cx.Np; e += gstride()) PW[e] = __ldcg(Rr + e) + bt * __ldcg(Po + e);
+                }
+            } else if (first) {
+                pass(true, pc, -1, -1, -1, -1, noprep, epiU);
+            } else {
+                pass(true, B_R, po, -1, -1, -1, combine, epiU);
+            }
             if (!sync()) return it;
             // phase B: HP = B^T U + alpha D^T(phi''(D x) . D p); <p, HP>
             const S php = reduce(hess_vec_b(bx, pc, B_HP, nullptr), 5);
             if (!alive) return it;
-            passes += 2;
+            passes += gram() ? 1 : 2;
             if (!Sc::finite(php)) {
                 if (tid() == 0) raise(ST_NONFINITE);
                 alive = false;
@@ -843,8 +1084,17 @@ struct Eng {
         for (int e = lane; e < CKK; e += 32) zp[e] = Sc::zero();
         // phase K1: U = B v, V = B x - y (image pixels only: phase K2 reads
         // interiors).  The stages of v and then of x run through the same
-        // double buffer.
-        if (!tmafail && alive) {
+        // double buffer.  On the FFT path: two passes.
+        if (kFFT && cx.fft) {
+            pass(true, bv, -1, -1, -1, -1, noprep, [=](int c, int gi, int gj, long long, int, T v, T) {
+                U[pidx(c, gi, gj)] = v;
+                return T(0);
+            });
+            pass(true, bx, -1, -1, -1, B_Y, noprep, [=](int c, int gi, int gj, long long, int, T v, T yv) {
+                V[pidx(c, gi, gj)] = v - yv;
+                return T(0);
+            });
+        } else if (!tmafail && alive) {
             if (lane == 0) fence_proxy_async();
             for (int s = gw(); s < cx.nstrips; s += TW()) {
                 int c, row0, col0;
@@ -1133,8 +1383,8 @@ struct Eng {
 
 // The program of one call (selected by jb.mode) on one problem; every CTA of
 // the problem's grid or group runs it.
-template <typename T>
-__device__ __forceinline__ void run_program(Eng<T> &e, const Ctx<T> &cx, const Job<T> &jb)
+template <typename T, bool FFTP>
+__device__ __forceinline__ void run_program(Eng<T, FFTP> &e, const Ctx<T> &cx, const Job<T> &jb)
 {
     const bool lead = threadIdx.x == 0 && e.bid == 0;
     long long passes = 0;
@@ -1230,7 +1480,7 @@ __device__ __forceinline__ void run_program(Eng<T> &e, const Ctx<T> &cx, const J
 #define ADP_KERNEL_SMEM extern __shared__ __align__(128) unsigned char smem_raw[]
 
 // One problem per launch: the launch record lives in parameter space.
-template <typename T>
+template <typename T, bool FFTP = false>
 __global__ void __launch_bounds__(MAXNW * 32, 1) adp_kernel(const __grid_constant__ Ctx<T> cx,
                                                             const __grid_constant__ Job<T> jb)
 {
@@ -1240,8 +1490,8 @@ __global__ void __launch_bounds__(MAXNW * 32, 1) adp_kernel(const __grid_constan
         return;
     }
     if (threadIdx.x == 0 && blockIdx.x == 0) cx.out->t_start = (long long)globaltimer_ns();
-    Eng<T> e(cx, &cx, gridDim.x, blockIdx.x, smem_raw);
-    run_program<T>(e, cx, jb);
+    Eng<T, FFTP> e(cx, &cx, gridDim.x, blockIdx.x, smem_raw);
+    run_program<T, FFTP>(e, cx, jb);
     if (threadIdx.x == 0 && blockIdx.x == 0) cx.out->t_end = (long long)globaltimer_ns();
 }
 
@@ -1269,8 +1519,8 @@ __global__ void __launch_bounds__(MAXNW * 32, 1) adp_kernel_batched(const Ctx<T>
         return;
     }
     if (threadIdx.x == 0 && blockIdx.x == (unsigned)f0) cx.out->t_start = (long long)globaltimer_ns();
-    Eng<T> e(cx, ctxs + g, nb, (int)blockIdx.x - f0, smem_raw);
-    run_program<T>(e, cx, jobs[g]);
+    Eng<T, false> e(cx, ctxs + g, nb, (int)blockIdx.x - f0, smem_raw);
+    run_program<T, false>(e, cx, jobs[g]);
     if (threadIdx.x == 0 && blockIdx.x == (unsigned)f0) cx.out->t_end = (long long)globaltimer_ns();
 }
 
