@@ -102,18 +102,20 @@ int adp_bf16_grid_size(adp_problem *p);
 /* Operator path of the problem's later calls.  With enable = 1, every
  * application of B, B^T and A inside the library's calls (adp_apply_B/Bt,
  * the lower solve, the Hessian products of CG, the upper loss, the
- * kernel-gradient correlation's operator passes, MAID) is evaluated through
- * the convolution theorem: with periodic boundaries B x is the circular
- * convolution of x with k(u, v) = b[u + r, v + r] (Eq. 2.4), so
- * B x = F^-1(F(k) . F(x)) and B^T z = F^-1(conj(F(k)) . F(z)), with 2-D FFTs
- * in FP32 (radix-2, twiddles rounded once from double).  The cost per
- * application no longer grows with K^2.  Only for ADP_F32 problems whose H
- * and W are powers of two (2..8192) and whose rows and columns fit the
- * kernel's shared memory; otherwise ADP_EINVAL and the path is unchanged.  The
- * first enable allocates 5 x C x H x W floats of workspace (kept until the
- * problem is destroyed).  enable = 0 returns to the direct correlation.
- * A batch (adp_batch_*) of one problem follows the problem's path; batches of
- * several problems use the direct correlation. */
+ * kernel-gradient correlation, MAID) is evaluated through the convolution
+ * theorem: with periodic boundaries B x is the circular convolution of x with
+ * k(u, v) = b[u + r, v + r] (Eq. 2.4), so B x = F^-1(F(k) . F(x)),
+ * B^T z = F^-1(conj(F(k)) . F(z)) and B^T B x = F^-1(|F(k)|^2 . F(x)), with
+ * 2-D FFTs in FP32 (radix-2, twiddles rounded once from double); the
+ * kernel-gradient correlation's K^2 lag sums are read off the inverse
+ * transform of F(B v) conj(F(x)) + F(B x - y) conj(F(v)).  The cost no longer
+ * grows with K^2.  Only for ADP_F32 problems whose H and W are powers of two
+ * (2..8192) and whose rows and columns fit the kernel's shared memory;
+ * otherwise ADP_EINVAL and the path is unchanged.  The first enable allocates
+ * 10 x C x H x W floats of workspace (kept until the problem is destroyed).
+ * enable = 0 returns to the direct correlation.  A batch (adp_batch_*) of one
+ * problem follows the problem's path; batches of several problems use the
+ * direct correlation. */
 adp_status adp_set_fft(adp_problem *p, int enable);
 int adp_fft_enabled(adp_problem *p);
 

@@ -88,7 +88,7 @@ struct adp_problem {
     TcTimes tc_times;
     // FFT operator path (adp_set_fft): on/off, log2 sizes, column block, buffers
     int fft, flogH, flogW, fcb, frb;
-    float2 *fz, *fs, *ftw;  // complex scratch image, kernel spectrum, twiddles (H/2 then W/2)
+    float2 *fz, *fs, *fy, *ftw;  // complex scratch, kernel spectrum, second spectrum, twiddles (H/2, W/2)
     float *fout, *fc;       // correlation of the last FFT pass; B^T y of the current lower solve
 };
 
@@ -187,7 +187,7 @@ static Ctx<T> make_ctx(const adp_problem *p)
     c.timeout_ns = (long long)(to * 1e9);
     if (p->fft) {
         c.fft = 1; c.flogH = p->flogH; c.flogW = p->flogW; c.fcb = p->fcb; c.frb = p->frb;
-        c.fz = p->fz; c.fs = p->fs; c.fout = (T *)p->fout; c.fc = (T *)p->fc;
+        c.fz = p->fz; c.fs = p->fs; c.fy = p->fy; c.fout = (T *)p->fout; c.fc = (T *)p->fc;
         c.ftwH = p->ftw; c.ftwW = p->ftw + q.H / 2;
     }
     return c;
@@ -266,7 +266,7 @@ void adp_problem_destroy(adp_problem *p)
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
     tc_plan_destroy(p->tc);
-    void *fptrs[] = {p->fz, p->fs, p->ftw, p->fout, p->fc};
+    void *fptrs[] = {p->fz, p->fs, p->fy, p->ftw, p->fout, p->fc};
     for (void *q : fptrs) if (q) cudaFree(q);
     free(p->a_host);
     free(p);
@@ -508,6 +508,7 @@ adp_status adp_set_fft(adp_problem *p, int enable)
         const size_t n = (size_t)q.C * q.H * q.W;
         CK(cudaMalloc((void **)&p->fz, n * sizeof(float2)));
         CK(cudaMalloc((void **)&p->fs, n * sizeof(float2)));
+        CK(cudaMalloc((void **)&p->fy, n * sizeof(float2)));
         CK(cudaMalloc((void **)&p->fout, n * sizeof(float)));
         CK(cudaMalloc((void **)&p->fc, n * sizeof(float)));
         CK(cudaMalloc((void **)&p->ftw, (size_t)(q.H / 2 + q.W / 2) * sizeof(float2)));

@@ -542,7 +542,7 @@ struct Ctx {
     long long timeout_ns;
     // FFT operator path (FP32 problems with power-of-two H and W; fft = 0: direct)
     int fft, flogH, flogW, fcb, frb;   // log2 H, log2 W, columns per column block, rows per row batch
-    float2 *fz, *fs;                   // complex scratch image and kernel spectrum, C x H x W each
+    float2 *fz, *fs, *fy;              // complex scratch image, kernel spectrum, second spectrum; C x H x W each
     T *fout;                           // the correlation of the last FFT pass, dense C x H x W
     T *fc;                             // B^T y_delta of the current lower solve (FFT path), dense
     const float2 *ftwH, *ftwW;         // twiddles exp(-2 pi i j / n), j < n/2, for n = H and n = W

@@ -380,52 +380,115 @@ struct Eng {
                     return v;
                 });
             if (!sync()) return false;
-            fft_columns(FM_B, true);
+            fft_columns(FM_B, CM_STORE, cx.fs);
             return sync();
         } else {
             return false;
         }
     }
 
-    // Column transforms over cx.fz in blocks of cx.fcb columns: forward, then
-    // times the spectrum (FM_B), its conjugate (FM_BT) or its squared modulus
-    // (FM_GRAM, the operator B^T B), and inverse back into cx.fz; or
-    // (spec_only) the forward transform alone into cx.fs.
-    __device__ void fft_columns(int fm, bool spec_only)
+    // Column transforms over cx.fz (or, for CM_INV, over src) in blocks of
+    // cx.fcb columns.  After the forward transform of the block:
+    //   CM_CONV   times the spectrum (FM_B), its conjugate (FM_BT) or its squared
+    //             modulus (FM_GRAM, the operator B^T B), inverse, back into cx.fz;
+    //   CM_STORE  dst = the transform;
+    //   CM_XSTORE dst = src . conj(transform);  CM_XADD dst += src . conj(transform)
+    //             (cross-correlation spectra; dst may be src);
+    //   CM_INV    (no forward transform) the inverse of src's columns into cx.fz.
+    enum { CM_CONV = 0, CM_STORE = 1, CM_XSTORE = 2, CM_XADD = 3, CM_INV = 4 };
+    __device__ void fft_columns(int fm, int cm = CM_CONV, float2 *dst = nullptr, const float2 *src = nullptr)
     {
         float2 *a = fft_scratch();
         const int H = cx.H, W = cx.W, lh = cx.flogH, CB = cx.fcb, lcb = __ffs(CB) - 1, nbc = W / CB;
+        const int n = H * CB, bd = blockDim.x;
         for (int cbi = bid; cbi < cx.C * nbc; cbi += nblk) {
             const int c = cbi / nbc, j0 = (cbi - c * nbc) * CB;
             const long long o = (long long)c * H * W + j0;
             auto gidx = [=](int e) { return (long long)(e >> lcb) * W + (e & (CB - 1)); };
             auto sidx = [=](int e) { return fslot(e & (CB - 1), e >> lcb, CB); };
-            const float2 *zc = cx.fz + o;
-            fft_copy(H * CB, [=](int e) { return __ldcg(zc + gidx(e)); }, [=](int e, float2 v) { a[sidx(e)] = v; });
+            const float2 *zc = (cm == CM_INV ? src : cx.fz) + o;
+            fft_copy(n, [=](int e) { return __ldcg(zc + gidx(e)); }, [=](int e, float2 v) { a[sidx(e)] = v; });
             __syncthreads();
-            fft_stages<true>(a, H, lh, CB, cx.ftwH, false);
-            if (spec_only) {
-                float2 *sc = cx.fs + o;
-                fft_copy(H * CB, [=](int e) { return a[sidx(e)]; }, [=](int e, float2 v) { sc[gidx(e)] = v; });
+            if (cm != CM_INV) fft_stages<true>(a, H, lh, CB, cx.ftwH, false);
+            if (cm == CM_STORE) {
+                float2 *dc = dst + o;
+                fft_copy(n, [=](int e) { return a[sidx(e)]; }, [=](int e, float2 v) { dc[gidx(e)] = v; });
                 __syncthreads();
                 continue;
             }
-            const float2 *sc = cx.fs + o;
-            const float sgn = fm == FM_B ? 1.f : -1.f;
-            fft_copy(H * CB, [=](int e) { return __ldcg(sc + gidx(e)); },
-                     [=](int e, float2 sp) {
-                         const int sl = sidx(e);
-                         if (fm == FM_GRAM) {
-                             const float m2 = fmaf(sp.x, sp.x, sp.y * sp.y);
-                             a[sl] = make_float2(a[sl].x * m2, a[sl].y * m2);
-                         } else {
-                             a[sl] = cmul(a[sl], make_float2(sp.x, sgn * sp.y));
-                         }
-                     });
-            __syncthreads();
+            if (cm == CM_XSTORE || cm == CM_XADD) {
+                float2 *dc = dst + o;
+                const float2 *sc = src + o;
+                for (int e0 = tid(); e0 < n; e0 += FU * bd) {
+                    float2 sv[FU], dv[FU];
+#pragma unroll
+                    for (int u = 0; u < FU; ++u) {
+                        const long long g = gidx(min(e0 + u * bd, n - 1));
+                        sv[u] = __ldcg(sc + g);
+                        dv[u] = cm == CM_XADD ? __ldcg(dc + g) : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < FU; ++u) {
+                        const int e = e0 + u * bd;
+                        if (e < n) {
+                            const float2 t = a[sidx(e)];
+                            const float2 pr = cmul(sv[u], make_float2(t.x, -t.y));
+                            dc[gidx(e)] = make_float2(dv[u].x + pr.x, dv[u].y + pr.y);
+                        }
+                    }
+                }
+                __syncthreads();
+                continue;
+            }
+            if (cm == CM_CONV) {
+                const float2 *sc = cx.fs + o;
+                const float sgn = fm == FM_B ? 1.f : -1.f;
+                fft_copy(n, [=](int e) { return __ldcg(sc + gidx(e)); },
+                         [=](int e, float2 sp) {
+                             const int sl = sidx(e);
+                             if (fm == FM_GRAM) {
+                                 const float m2 = fmaf(sp.x, sp.x, sp.y * sp.y);
+                                 a[sl] = make_float2(a[sl].x * m2, a[sl].y * m2);
+                             } else {
+                                 a[sl] = cmul(a[sl], make_float2(sp.x, sgn * sp.y));
+                             }
+                         });
+                __syncthreads();
+            }
             fft_stages<false>(a, H, lh, CB, cx.ftwH, true);
             float2 *zw = cx.fz + o;
-            fft_copy(H * CB, [=](int e) { return a[sidx(e)]; }, [=](int e, float2 v) { zw[gidx(e)] = v; });
+            fft_copy(n, [=](int e) { return a[sidx(e)]; }, [=](int e, float2 v) { zw[gidx(e)] = v; });
+            __syncthreads();
+        }
+    }
+
+    // forward row transforms of padded buffer img into cx.fz
+    __device__ void fft_rows_img(int img)
+    {
+        const T *src = buf(img);
+        const long long HWp = cx.HWp;
+        const int Wp = cx.Wp, Gy = cx.Gy, Gx = cx.Gx;
+        for (int r0 = bid * cx.frb; r0 < cx.C * cx.H; r0 += nblk * cx.frb)
+            fft_rows_fwd(r0, [=](int c, int i, int j) {
+                return (float)__ldcg(src + c * HWp + (long long)(i + Gy) * Wp + Gx + j);
+            });
+    }
+
+    // inverse row transforms of cx.fz, real part / (H W) into out (dense)
+    __device__ void fft_rows_inv(T *out)
+    {
+        float2 *a = fft_scratch();
+        const int H = cx.H, W = cx.W, lw = cx.flogW, RB = cx.frb;
+        const float scale = 1.f / ((float)H * (float)W);
+        for (int r0 = bid * RB; r0 < cx.C * H; r0 += nblk * RB) {
+            const float2 *z = cx.fz + (long long)r0 * W;
+            fft_copy(RB * W, [=](int e) { return __ldcg(z + e); },
+                     [=](int e, float2 v) { a[fslot(e >> lw, e & (W - 1), RB)] = v; });
+            __syncthreads();
+            fft_stages<false>(a, W, lw, RB, cx.ftwW, true);
+            T *o = out + (long long)r0 * W;
+            fft_copy(RB * W, [=](int e) { return a[fslot(e >> lw, e & (W - 1), RB)]; },
+                     [=](int e, float2 v) { o[e] = v.x * scale; });
             __syncthreads();
         }
     }
@@ -436,31 +499,37 @@ struct Eng {
     __device__ bool fft_conv(int fm, int img, T *dst = nullptr)
     {
         if constexpr (kFFT) {
-            float2 *a = fft_scratch();
-            const int H = cx.H, W = cx.W, lw = cx.flogW, RB = cx.frb;
-            const T *src = buf(img);
-            const long long HWp = cx.HWp;
-            const int Wp = cx.Wp, Gy = cx.Gy, Gx = cx.Gx;
-            for (int r0 = bid * RB; r0 < cx.C * H; r0 += nblk * RB)
-                fft_rows_fwd(r0, [=](int c, int i, int j) {
-                    return (float)__ldcg(src + c * HWp + (long long)(i + Gy) * Wp + Gx + j);
-                });
+            fft_rows_img(img);
             if (!sync()) return false;
-            fft_columns(fm, false);
+            fft_columns(fm);
             if (!sync()) return false;
-            T *out = dst ? dst : cx.fout;
-            const float scale = 1.f / ((float)H * (float)W);
-            for (int r0 = bid * RB; r0 < cx.C * H; r0 += nblk * RB) {
-                const float2 *z = cx.fz + (long long)r0 * W;
-                fft_copy(RB * W, [=](int e) { return __ldcg(z + e); },
-                         [=](int e, float2 v) { a[fslot(e >> lw, e & (W - 1), RB)] = v; });
-                __syncthreads();
-                fft_stages<false>(a, W, lw, RB, cx.ftwW, true);
-                T *o = out + (long long)r0 * W;
-                fft_copy(RB * W, [=](int e) { return a[fslot(e >> lw, e & (W - 1), RB)]; },
-                         [=](int e, float2 v) { o[e] = v.x * scale; });
-                __syncthreads();
+            fft_rows_inv(dst ? dst : cx.fout);
+            return sync();
+        } else {
+            return false;
+        }
+    }
+
+    // FFT path of the kernel-gradient correlation: with U = B v and
+    // V = B x - y in their buffers, out[c, p, q] = sum_n U[n] x[n - d] +
+    // V[n] v[n - d] at the lag d = (p - r, q - r) is the inverse transform of
+    // F(U) conj(F(x)) + F(V) conj(F(v)), read at d (mod H, W).  Into cx.fout.
+    __device__ bool fft_cross(int bx, int bv)
+    {
+        if constexpr (kFFT) {
+            const int steps[4] = {B_U, bx, B_V, bv};
+            const int modes[4] = {CM_STORE, CM_XSTORE, CM_STORE, CM_XADD};
+            float2 *dsts[4] = {cx.fs, cx.fs, cx.fy, cx.fs};
+            const float2 *srcs[4] = {nullptr, cx.fs, nullptr, cx.fy};
+            for (int k = 0; k < 4; ++k) {
+                fft_rows_img(steps[k]);
+                if (!sync()) return false;
+                fft_columns(FM_B, modes[k], dsts[k], srcs[k]);
+                if (!sync()) return false;
             }
+            fft_columns(FM_B, CM_INV, nullptr, cx.fs);
+            if (!sync()) return false;
+            fft_rows_inv(cx.fout);
             return sync();
         } else {
             return false;
@@ -1132,6 +1201,18 @@ struct Eng {
             }
         }
         if (!sync()) return 0.0;
+        if (gram()) {   // FFT path: all lags from one spectrum product, then sign and Sobolev term
+            if (!fft_cross(bx, bv)) return 0.0;
+            for (long long e = gstart(); e < CKK; e += gstride()) {
+                const int c = (int)(e / KK), pq = (int)(e - (long long)c * KK), p = pq / K, q = pq - p * K;
+                const int i = ((p - r) % H + H) % H, j = ((q - r) % W + W) % W;
+                double zz = (double)__ldcg(cx.fout + (long long)c * cx.HW + (long long)i * W + j);
+                if (negate) zz = -zz;
+                if (add_r) zz += grad_sobolev_elem(b, (int)e);
+                zout[e] = (T)zz;
+            }
+            passes += 4;
+        } else {
         // phase K2: lag sums of this warp's strips, by stages of PC lag rows.
         // Lag p and strip row m read tile row m + 2r - p, so the stage of lags
         // p0 .. p0+PC-1 holds tile rows from 2r - p0 - PC + 1 (NX rows) of x
@@ -1233,6 +1314,7 @@ struct Eng {
             }
         }
         passes += 4;   // B v, B x and the two lag correlations
+        }
         if (!sync()) return 0.0;
         S s = Sc::zero();
         for (int e = tid(); e < CKK; e += blockDim.x) {
