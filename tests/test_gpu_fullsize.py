@@ -124,6 +124,39 @@ def test_cross_term_identity(name):
     assert abs(lhs - rhs) <= 1e-4 * max(abs(rhs), 1e-30), (lhs, rhs)
 
 
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_fft_path_sampled(name):
+    """The FFT operator path at full size: B x and B^T x, and one FISTA update
+    (which takes B^T B y through |F(k)|^2 and B^T y_delta once), on sampled
+    outputs.  Tolerance for an FFT application: max(1e-6, 2 log2(H W) u)."""
+    pr = pair_for(name)
+    C, H, W = pr.inst.shape
+    K = pr.inst.K
+    tol = max(1e-6, 2 * np.log2(H * W) * U32)
+    pr.prob.set_fft(True)
+    try:
+        x = pr.rounded(pr.inst.x_true)
+        b = pr.rounded(pr.inst.b_true)
+        idx = sample_idx(C, H, W, 200, 4)
+        out = pr.n(pr.prob.apply_B(pr.t(b), pr.t(x)))
+        assert rel(take(out, idx), pr.P.conv_at(b, x, idx)) <= tol
+        outT = pr.n(pr.prob.apply_Bt(pr.t(b), pr.t(x)))
+        assert rel(take(outT, idx), pr.P.conv_adj_at(b, x, idx)) <= tol
+        ba = pr.a
+        xg = pr.t(pr.y)
+        it, _, _ = pr.prob.lower_solve(pr.t(ba), xg, 0.0, 1)
+        assert it == 1
+        idx = sample_idx(C, H, W, 12 if K > 40 else 40, 5)
+        tau = np.array([1.0 / pr.P.lipschitz(ba, c) for c in range(C)])
+        g = pr.P.grad_h_at(ba, pr.y, pr.y, idx)
+        x1 = np.array([pr.y[c, i, j] for c, i, j in idx]) - tau[[c for c, _, _ in idx]] * g
+        assert rel(take(pr.n(xg), idx), x1) <= 1e-6
+    finally:
+        pr.prob.set_fft(False)
+
+
 def test_free_large_problems():
     for p in _CACHE.values():
         p.prob.close()
