@@ -37,6 +37,8 @@
 
 namespace adp {
 
+cudaError_t optin_dynamic_smem(const void *fn, int maxsmem);   // adp.cu
+
 namespace {
 
 constexpr int TM = 128, TN = 32, KT = 64;   // tile rows, tile columns, band width (BF16 elements)
@@ -410,7 +412,10 @@ int tc_plan_create(int C, int H, int W, int K, int device, TcPlan **out, char *e
     TCK(cudaEventCreate(&p->e1));
     TCK(cudaEventCreate(&p->e2));
     TCK(cudaMemset(p->xb, 0, xbytes));
-    TCK(cudaFuncSetAttribute(tc_corr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem));
+    // the device's whole opt-in size rather than this plan's: the attribute is
+    // shared by every plan, and a smaller value set for a later plan (smaller K)
+    // would make the launches of an earlier, larger one fail
+    TCK(optin_dynamic_smem((const void *)tc_corr, maxsmem));
     int nsm = 0, occ = 0;
     TCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
     TCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tc_corr, NTHREADS, p->smem));

@@ -98,3 +98,18 @@ def test_bf16_rejects_unsupported_problems():
         big.prob.apply_B_bf16(big.t(np.zeros((1, 35, 35))), big.t(np.zeros((1, 64, 64))))
     assert e.value.status == adp.ADP_EINVAL
     big.prob.close()
+
+
+def test_bf16_problems_with_different_kernel_sizes_coexist():
+    """A plan made later for a smaller K must not shrink what an earlier,
+    larger plan launches with (the shared-memory attribute is per kernel)."""
+    big = Pair(instance(1, 96, 64, 31, 3), prec=adp.ADP_F32)
+    small = Pair(instance(1, 40, 32, 5, 4), prec=adp.ADP_F32)
+    rng = np.random.default_rng(11)
+    for pr, (C, H, W, K) in ((big, (1, 96, 64, 31)), (small, (1, 40, 32, 5)), (big, (1, 96, 64, 31))):
+        x = pr.rounded(rng.standard_normal((C, H, W)))
+        b = pr.rounded(rng.standard_normal((C, K, K)) / K)
+        out = pr.n(pr.prob.apply_B_bf16(pr.t(b), pr.t(x)))
+        assert rel(out, pr.P.conv(oracle.bf16_round(b), oracle.bf16_round(x))) <= max(1e-6, 4 * K * U32)
+    big.prob.close()
+    small.prob.close()
