@@ -112,7 +112,8 @@ int adp_bf16_grid_size(adp_problem *p);
  * grows with K^2.  Only for ADP_F32 problems whose H and W are powers of two
  * (2..8192) and whose rows and columns fit the kernel's shared memory;
  * otherwise ADP_EINVAL and the path is unchanged.  The first enable allocates
- * 10 x C x H x W floats of workspace (kept until the problem is destroyed).
+ * 32 bytes per value, C x H x W x 32 bytes in all (three complex images and two
+ * real ones; kept until the problem is destroyed).
  * enable = 0 returns to the direct correlation.  A batch (adp_batch_*) of one
  * problem follows the problem's path; batches of several problems use the
  * direct correlation. */
