@@ -69,6 +69,8 @@ WORKLOAD_SPECS = {
                       cpu_iters=4000, cpu_crop=None),
     "rgb512_k31": dict(name="rgb512_k31_gauss_perturbed", fn="rgb512_k31", dtype="f32", eps_stop=1e-4,
                        max_upper=40, cpu_iters=6, cpu_crop=None, eps0=1e-3, step0=1e-6),
+    "paper2d_motion": dict(name="paper2d_motion_sqrt_tv_fp64", fn="paper2d_motion", dtype="f64", eps_stop=1e-6,
+                           max_upper=30, cpu_iters=20, cpu_crop=None, eps0=1e-2, step0=1e-3),
     "rgb2048_k63": dict(name="rgb2048_k63_motion_gauss", fn="rgb2048_k63", dtype="f32", eps_stop=1e-3,
                         max_upper=20, cpu_iters=2, cpu_crop=192, eps0=1e-2, step0=1e-7),
 }
@@ -135,6 +137,14 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def lower_params(inst):
+    """Regulariser and weights of an instance (the 256^2/512^2/2048^2 workloads:
+    Huber TV with gamma 1e-2, alpha 1e-2, beta 0.3, full H^1 norm)."""
+    p = inst.params
+    return dict(alpha=p.get("alpha", 1e-2), reg_param=p.get("reg_param", 1e-2),
+                sqrt_tv=p.get("reg", "huber") == "sqrt", beta=p.get("beta", 0.3), w0=p.get("w0", 1.0))
+
+
 def oracle_sample(inst, iters, crop=None):
     """FP64 oracle (as it stands, single thread) running FISTA iterations of the
     lower level on the same workload (or on a centred crop x crop window of it,
@@ -147,7 +157,9 @@ def oracle_sample(inst, iters, crop=None):
         i0, j0 = (H - crop) // 2, (W - crop) // 2
         y = y[:, i0:i0 + crop, j0:j0 + crop].copy()
         H = W = crop
-    P = oracle.Problem(C, H, W, inst.K, alpha=1e-2, reg_param=1e-2, beta=0.3)
+    lp = lower_params(inst)
+    P = oracle.Problem(C, H, W, inst.K, alpha=lp["alpha"], reg_param=lp["reg_param"],
+                       reg=oracle.REG_SQRT if lp["sqrt_tv"] else oracle.REG_HUBER, beta=lp["beta"], w0=lp["w0"])
     t = time.perf_counter()
     P.fista(inst.a, y, y, eps=0.0, max_iters=iters)
     dt = time.perf_counter() - t
@@ -442,8 +454,13 @@ def run_ours(args):
     tdt = torch.float64 if f64 else torch.float32
     y = torch.tensor(inst.y, dtype=tdt, device=dev)
     a = torch.tensor(inst.a, dtype=tdt, device=dev)
-    prob = adp.Problem(adp.Params(C, H, W, K, alpha=1e-2, reg_param=1e-2, beta=0.3,
+    lp = lower_params(inst)
+    prob = adp.Problem(adp.Params(C, H, W, K, alpha=lp["alpha"], reg_param=lp["reg_param"],
+                                  reg=adp.ADP_REG_SQRT_TV if lp["sqrt_tv"] else adp.ADP_REG_HUBER_TV,
+                                  beta=lp["beta"], sobolev_w0=lp["w0"],
                                   prec=adp.ADP_F64 if f64 else adp.ADP_F32), y, a)
+    if lp["sqrt_tv"]:
+        args.no_torch_baseline = True   # the PyTorch MAID baseline implements the Huber TV only
     fft = args.operator_path == "fft"
     if fft:
         prob.set_fft(True)
@@ -567,8 +584,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": spec["dtype"], "data": "synthetic",
-        "config": {"workload": spec["name"] + ("_fft" if fft else ""), "C": C, "H": H, "W": W, "K": K, "alpha": 1e-2, "huber": 1e-2,
-                   "beta": 0.3, "maid_eps0": EPS0, "maid_step0": STEP0, "eps_stop": EPS_STOP,
+        "config": {"workload": spec["name"] + ("_fft" if fft else ""), "C": C, "H": H, "W": W, "K": K, "alpha": lp["alpha"], ("sqrt_tv_nu" if lp["sqrt_tv"] else "huber"): lp["reg_param"],
+                   "beta": lp["beta"], "sobolev_w0": lp["w0"], "maid_eps0": EPS0, "maid_step0": STEP0, "eps_stop": EPS_STOP,
                    "max_upper": MAX_UPPER, "step": "one MAID run to the stop rule",
                    "l2": "flushed between timed runs (256 MB write)", "parallelism": f"replicas x{world}"},
         "maid": {"time_to_tolerance_s": tot_ms_max / args.steps / 1e3,

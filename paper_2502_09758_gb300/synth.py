@@ -173,6 +173,35 @@ def rgb2048_k63(seed=0):
                          alpha=1e-2, reg_param=1e-2, beta=0.3, dtype="f32")
 
 
+def diagonal_motion_kernel(K):
+    """K x K motion blur along the main diagonal, equal weights summing to 1
+    (the paper's 5 x 5 motion kernel of Sec. 4.2 has its non-zero entries on
+    the diagonal; the weights are not given)."""
+    return np.eye(K) / K
+
+
+def paper2d_motion(seed=0):
+    """The paper's 2D deblurring setting (Sec. 4.2) on a synthetic image:
+    300 x 400 RGB, the 5 x 5 diagonal motion blur as the generating kernel, as
+    A's kernel and as b_0, noise 0.02; sqrt-smoothed TV with nu = 1e-4,
+    alpha 0.6, beta 0.3 on the H^1 seminorm (w0 = 0); run in float64 (the
+    stop threshold is 1e-6)."""
+    k = diagonal_motion_kernel(5)
+    return make_instance("paper2d_motion", 3, 300, 400, k, k, 0.02, seed,
+                         alpha=0.6, reg_param=1e-4, reg="sqrt", beta=0.3, w0=0.0, dtype="f64")
+
+
+def paper2d_semiblind(seed=0):
+    """Semi-blind variant of Sec. 4.2: the data is blurred by the motion kernel
+    followed by a 5 x 5 Gaussian with sigma 0.5, and only the motion kernel is
+    known (A's kernel and b_0).  The composed kernel is cropped to 5 x 5 and
+    renormalised so that a 5 x 5 b can represent it."""
+    km = diagonal_motion_kernel(5)
+    kt = _smooth_kernel_combine(km, gaussian_kernel(5, 0.5))
+    return make_instance("paper2d_semiblind", 3, 300, 400, kt, km, 0.02, seed,
+                         alpha=0.6, reg_param=1e-4, reg="sqrt", beta=0.3, w0=0.0, dtype="f64")
+
+
 def batch_mixed(n=64, seed=0, size_range=(128, 512), ks=(5, 9, 15, 21, 31)):
     """n independent RGB problems of uneven size and kernel (Gaussian or motion)."""
     rng = np.random.default_rng(20_000 + seed)
@@ -202,4 +231,6 @@ WORKLOADS = {
     "rgb256_k15_motion": rgb256_k15,
     "rgb512_k31_gauss_perturbed": rgb512_k31,
     "rgb2048_k63_motion_gauss": rgb2048_k63,
+    "paper2d_motion": paper2d_motion,
+    "paper2d_semiblind": paper2d_semiblind,
 }

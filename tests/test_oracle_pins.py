@@ -512,3 +512,4 @@ def test_bf16_round_matches_torch_conversion():
     v = (rng.standard_normal(50000) * np.exp(rng.uniform(-30, 30, 50000))).astype(np.float32)
     t = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
     np.testing.assert_array_equal(oracle.bf16_round(v), t)
+
