@@ -46,3 +46,21 @@ def test_library_has_no_cpu_fallback_symbols(lib_path):
     lib = ctypes.CDLL(lib_path)
     for name in ("orc_conv", "orc_fista", "orc_maid_step"):
         assert not hasattr(lib, name)
+
+
+def test_null_handles_are_rejected_before_any_device_work(lib_path):
+    """Argument checks come first: a null problem gives ADP_EINVAL (and the
+    queries their neutral values) without touching a device, so this runs
+    on a machine without one."""
+    from paper_2502_09758_gb300 import adp
+    lib = adp.load_library(lib_path)
+    nul = None
+    assert lib.adp_apply_B_bf16(nul, nul, nul, nul) == adp.ADP_EINVAL
+    assert lib.adp_apply_Bt_bf16(nul, nul, nul, nul) == adp.ADP_EINVAL
+    assert lib.adp_set_fft(nul, 1) == adp.ADP_EINVAL
+    assert lib.adp_set_fft(nul, 0) == adp.ADP_EINVAL
+    assert lib.adp_fft_enabled(nul) == 0
+    assert lib.adp_bf16_grid_size(nul) == 0
+    assert lib.adp_bf16_prep_ms_last(nul) == -1.0
+    assert lib.adp_apply_B(nul, nul, nul, nul) == adp.ADP_EINVAL
+    assert b"null problem" in lib.adp_last_error()
