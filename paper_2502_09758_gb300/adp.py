@@ -250,6 +250,34 @@ class Problem:
     def fft_enabled(self) -> bool:
         return bool(self.lib.adp_fft_enabled(self.handle))
 
+    def choose_operator_path(self, b, x, iters=8, reps=2):
+        """Autotune the operator path: time FISTA updates (adp_lower_solve with
+        eps = 0, launches of ``iters`` and ``2 iters`` updates, so that the
+        per-solve set-up cancels) on the direct path and, where the problem
+        admits it, on the FFT path; keep the faster per update for later calls.
+        Returns {"path": "direct" | "fft", "direct_ms": ..., "fft_ms": ...}
+        (per update, best of ``reps``)."""
+        per = {}
+        for path in ("direct", "fft"):
+            try:
+                self.set_fft(path == "fft")
+            except AdpError as e:
+                if e.status != ADP_EINVAL:
+                    raise
+                continue
+            best = float("inf")
+            for _ in range(reps):
+                t = []
+                for n in (iters, 2 * iters):
+                    xs = x.clone()
+                    self.lower_solve(b, xs, 0.0, n)
+                    t.append(self.last_kernel_ms())
+                best = min(best, (t[1] - t[0]) / iters)
+            per[path] = best
+        choice = min(per, key=per.get)
+        self.set_fft(choice == "fft")
+        return {"path": choice, **{f"{k}_ms": v for k, v in per.items()}}
+
     def bf16_prep_ms(self) -> float:
         return float(self.lib.adp_bf16_prep_ms_last(self.handle))
 
