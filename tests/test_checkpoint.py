@@ -5,7 +5,7 @@ import json
 import numpy as np
 import torch
 
-from paper_2502_09758_gb300 import adp
+from paper_2502_09758_gb300 import adp, runtime
 
 
 def _state():
@@ -22,8 +22,8 @@ def test_checkpoint_round_trip_is_exact(tmp_path):
     x = torch.from_numpy(rng.standard_normal((3, 8, 6)))
     q = torch.from_numpy(rng.standard_normal((3, 8, 6)))
     p = tmp_path / "ck.npz"
-    adp.save_maid_checkpoint(p, s, b, x, q, workload="t", seed=3)
-    s2, b2, x2, q2, meta = adp.load_maid_checkpoint(p, device="cpu")
+    runtime.save_maid_checkpoint(p, s, b, x, q, workload="t", seed=3)
+    s2, b2, x2, q2, meta = runtime.load_maid_checkpoint(p, device="cpu")
     for name, _ in adp.adp_maid_state._fields_:
         assert getattr(s2, name) == getattr(s, name), name
     assert b2.dtype == torch.float32 and x2.dtype == torch.float64
@@ -34,7 +34,7 @@ def test_checkpoint_round_trip_is_exact(tmp_path):
 def test_maid_log_records(tmp_path):
     s = _state()
     x_true = np.zeros((1, 2, 2))
-    log = adp.MaidLog(tmp_path / "run.jsonl", x_true=x_true)
+    log = runtime.MaidLog(tmp_path / "run.jsonl", x_true=x_true)
     rec = log.record(s, True, 1.5, x=torch.full((1, 2, 2), 0.1, dtype=torch.float64))
     log.record(s, False, 2.0)
     log.close()

@@ -5,7 +5,7 @@ fixed order)."""
 import pytest
 import torch
 
-from paper_2502_09758_gb300 import adp, synth
+from paper_2502_09758_gb300 import adp, runtime, synth
 from gpu_common import need_gpu
 
 pytestmark = pytest.mark.gpu
@@ -27,13 +27,13 @@ def test_resume_is_bit_exact(tmp_path, prec):
     b, x, q = a.clone(), y.clone(), torch.zeros_like(y)
     prob.maid_step(s, b, x, q)
     path = tmp_path / "step1.npz"
-    adp.save_maid_checkpoint(path, s, b, x, q)
-    log = adp.MaidLog(tmp_path / "run.jsonl", x_true=inst.x_true, b_true=inst.b_true)
+    runtime.save_maid_checkpoint(path, s, b, x, q)
+    log = runtime.MaidLog(tmp_path / "run.jsonl", x_true=inst.x_true, b_true=inst.b_true)
     for _ in range(2):
         acc = prob.maid_step(s, b, x, q)
         log.record(s, acc, 0.0, b=b, x=x)
     log.close()
-    s2, b2, x2, q2, _ = adp.load_maid_checkpoint(path)
+    s2, b2, x2, q2, _ = runtime.load_maid_checkpoint(path)
     for _ in range(2):
         prob.maid_step(s2, b2, x2, q2)
     assert torch.equal(b2, b) and torch.equal(x2, x) and torch.equal(q2, q)

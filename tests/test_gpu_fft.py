@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 import torch
 
-from paper_2502_09758_gb300 import adp, synth
+from paper_2502_09758_gb300 import adp, runtime, synth
 from gpu_common import Pair, need_gpu, psnr, rel
 
 pytestmark = pytest.mark.gpu
@@ -211,17 +211,17 @@ def test_fft_toggle_and_rejections():
 
 
 def test_operator_path_autotune_keeps_the_faster():
-    """choose_operator_path keeps the path with the lower measured cost per
+    """runtime.choose_operator_path keeps the path with the lower measured cost per
     FISTA update, and leaves the problem on it; a problem the FFT path does
     not admit stays direct."""
     pr = Pair(inst_for(3, 128, 128, 31), prec=adp.ADP_F32)
     b, x = pr.t(pr.rounded(pr.inst.a)), pr.t(pr.rounded(pr.inst.y))
-    r = pr.prob.choose_operator_path(b, x, iters=4, reps=1)
+    r = runtime.choose_operator_path(pr.prob, b, x, iters=4, reps=1)
     assert set(r) == {"path", "direct_ms", "fft_ms"}
     assert r["path"] == ("fft" if r["fft_ms"] < r["direct_ms"] else "direct")
     assert pr.prob.fft_enabled() == (r["path"] == "fft")
     pr.prob.close()
     q = Pair(inst_for(3, 70, 45, 7), prec=adp.ADP_F32)
-    r = q.prob.choose_operator_path(q.t(q.rounded(q.inst.a)), q.t(q.rounded(q.inst.y)), iters=4, reps=1)
+    r = runtime.choose_operator_path(q.prob, q.t(q.rounded(q.inst.a)), q.t(q.rounded(q.inst.y)), iters=4, reps=1)
     assert r["path"] == "direct" and "fft_ms" not in r and not q.prob.fft_enabled()
     q.prob.close()
