@@ -1,9 +1,13 @@
 #!/usr/bin/env python
 """Benchmark of the ADP-beta / MAID hot path on GB300.
 
-Workload: 256 x 256 RGB, 15 x 15 motion blur (length 11 at 30 deg; b_0 = the
-same blur at 20 deg), noise 0.02, Huber-TV lower level (alpha 1e-2, gamma 1e-2),
-Sobolev upper level (beta 0.3), FP32 operators with FP64 reductions.
+Headline workload: 2048 x 2048 RGB, 63 x 63 kernel (a 31 px motion blur at 30
+deg convolved with a Gaussian sigma 3), noise 0.01, Huber-TV lower level
+(alpha 1e-2, gamma 1e-2), Sobolev upper level (beta 0.3, a = b_0 = the
+generating kernel), FP32 operators with float-float reductions, the FFT
+operator path (real-to-complex FISTA and CG).  --workload rgb256_k15 measures
+the 256 x 256 RGB, 15 x 15 motion-blur workload on the direct path, and the
+other --workload values the other configurations.
 
 One step = one complete MAID run (Algorithm 2) from b_0 and x_0 = y until the
 stop rule of Sec. 4.2 fires (eps <= eps_stop) or MAX_UPPER upper iterations
@@ -38,7 +42,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MAID time-to-tolerance (s) vs plain FP32 GPU; Mpixel·iter/s of fused steps"
 UNIT = "Mvalue·iter/s (values = C·H·W; iters = FISTA + CG iterations)"
-WORKLOAD = "rgb256_k15_motion"
+WORKLOAD = "rgb2048_k63_motion_gauss"
 SM_COUNT, FP32_LANES = 152, 128
 # FFT path, bytes per value and convolution pass: row transforms read the
 # FP32 image and write complex values (4 + 8), the column phase reads the
@@ -71,9 +75,21 @@ WORKLOAD_SPECS = {
                        max_upper=40, cpu_iters=6, cpu_crop=None, eps0=1e-3, step0=1e-6),
     "paper2d_motion": dict(name="paper2d_motion_sqrt_tv_fp64", fn="paper2d_motion", dtype="f64", eps_stop=1e-6,
                            max_upper=30, cpu_iters=20, cpu_crop=None, eps0=1e-2, step0=1e-3),
+    # 2048^2: the steps that decrease ell lie near 1e-10 (||z||^2 ~ 1e8) and pass
+    # psi <= 0 only at eps <= 3e-3 (sufficient-decrease slack 2 ||grad g|| eps
+    # with ||grad g|| ~ 3.8); the stop threshold 1e-3 sits just above the FP32
+    # floor of ||grad_x h|| at this size (~6e-4)
     "rgb2048_k63": dict(name="rgb2048_k63_motion_gauss", fn="rgb2048_k63", dtype="f32", eps_stop=1e-3,
-                        max_upper=20, cpu_iters=2, cpu_crop=192, eps0=1e-2, step0=1e-7),
+                        max_upper=20, cpu_iters=6, cpu_crop=192, eps0=2e-3, step0=3e-10, path="fft"),
 }
+# algorithmic bytes per value of the FFT path's phases (FP32): a FISTA
+# iteration on the real-to-complex pipeline (row phase: half spectrum 4, y_k 4,
+# x_k 4 in, x_{k+1} 4, y_{k+1} 4, half spectrum 4 out; column phase: half
+# spectrum 4 + 4, |F(k)|^2 2, F(B^T y) 4: 38 in all), a CG iteration (direction update and
+# its forward rows 16, column phase 10, inverse rows with the Hessian 16, the
+# element-wise update of q and r 24), and any other convolution pass on the
+# complex pipeline (FFT_BYTES_PER_VALUE)
+R2C_FISTA_BYTES, R2C_CG_BYTES = 38, 66
 
 
 def peaks():
@@ -166,31 +182,78 @@ def oracle_sample(inst, iters, crop=None):
     return C * H * W * iters / dt / 1e6, dt
 
 
+def _oracle_worker(job):
+    """One process of the all-core oracle sample: FISTA iterations on one
+    crop (spawned process; imports the oracle afresh)."""
+    import time as _t
+    import oracle
+    C, H, W, K, lp, a, y, iters = job
+    P = oracle.Problem(C, H, W, K, alpha=lp["alpha"], reg_param=lp["reg_param"],
+                       reg=oracle.REG_SQRT if lp["sqrt_tv"] else oracle.REG_HUBER, beta=lp["beta"], w0=lp["w0"])
+    t = _t.perf_counter()
+    P.fista(a, y, y, eps=0.0, max_iters=iters)
+    return C * H * W * iters, _t.perf_counter() - t
+
+
+def oracle_sample_all_cores(inst, iters, crop=None, procs=None):
+    """The same oracle sample run on every host core at once: one process per
+    core (spawned), each on its own crop (shifted windows of the same
+    workload; the whole image when it is small enough).  Returns
+    (Mvalue*iter/s over the wall time of the slowest process, processes)."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    procs = procs or os.cpu_count() or 1
+    C, H, W = inst.shape
+    lp = lower_params(inst)
+    jobs = []
+    for k in range(procs):
+        if crop:
+            i0 = (k * 97) % (H - crop + 1)
+            j0 = (k * 61) % (W - crop + 1)
+            y = inst.y[:, i0:i0 + crop, j0:j0 + crop].copy()
+            jobs.append((C, crop, crop, inst.K, lp, inst.a, y, iters))
+        else:
+            jobs.append((C, H, W, inst.K, lp, inst.a, inst.y, iters))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        out = pool.map(_oracle_worker, jobs)
+    units = sum(u for u, _ in out)
+    wall = max(dt for _, dt in out)
+    return units / wall / 1e6, procs
+
+
 def run_reference(args):
-    """The reference arm: the FP64 CPU oracle on the host cores, bounded sample
-    per step (rank 0 only)."""
+    """The reference arm: the FP64 CPU oracle on the host cores, a bounded
+    sample of the same workload per step (rank 0 only): FISTA iterations of
+    the lower level, on a centred crop when the image is too large."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from paper_2502_09758_gb300 import synth
-    inst = synth.rgb256_k15(0)
-    per_step = 4
+    spec = WORKLOAD_SPECS[args.workload]
+    inst = getattr(synth, spec["fn"])(0)
+    per_step = 1 if spec["cpu_crop"] else 4
     for _ in range(args.warmup):
-        oracle_sample(inst, 1)
+        oracle_sample(inst, 1, spec["cpu_crop"])
     tot, units = 0.0, 0
     C, H, W = inst.shape
+    Hs = Ws = spec["cpu_crop"] or None
     for _ in range(args.steps):
-        _, dt = oracle_sample(inst, per_step)
+        _, dt = oracle_sample(inst, per_step, spec["cpu_crop"])
         tot += dt
-        units += C * H * W * per_step
+        units += C * (Hs or H) * (Ws or W) * per_step
     val = units / tot / 1e6
+    fft = args.operator_path == "fft" or (args.operator_path == "auto" and spec.get("path") == "fft")
+    where = (f"a centred {Hs}x{Ws} crop (same kernel) of the {C}x{H}x{W}, K={inst.K} workload" if Hs
+             else f"the {C}x{H}x{W}, K={inst.K} workload")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "C": C, "H": H, "W": W, "K": inst.K},
+            "data": "synthetic",
+            "config": {"workload": spec["name"] + ("_fft" if fft else ""), "C": C, "H": H, "W": W, "K": inst.K},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} FISTA iterations of the FP64 oracle per step on the "
-                                       f"{C}x{H}x{W}, K={inst.K} workload"},
+                             "sample": f"{per_step} FISTA iteration(s) of the FP64 oracle per step on {where}"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -204,15 +267,19 @@ def maid_run(prob, a, y, b_h=None, x_h=None):
     q = torch.zeros_like(x)
     st = prob.maid_init(eps=EPS0, delta=EPS0, step=STEP0, eps_stop=EPS_STOP)
     ms, iters, passes, ups, acc = 0.0, 0, 0, 0, 0
+    split = [0, 0]                      # FISTA and CG iterations
     for _ in range(MAX_UPPER):
         ok = prob.maid_step(st, b, x, q)
         ms += prob.last_kernel_ms()
         iters += st.ll_iters + st.cg_iters
+        split[0] += st.ll_iters
+        split[1] += st.cg_iters
         passes += prob.conv_passes_last()
         ups += 1
         acc += int(ok)
         if st.stopped or not ok:
             break
+    maid_run.split = tuple(split)
     return ms, iters, passes, ups, acc, b, x, st
 
 
@@ -292,13 +359,15 @@ def reduce_over_ranks(tot_ms, units, device=None):
     return float(tmax[0]), float(t[1])
 
 
-def torch_maid_run(inst, max_upper, dtype, dev):
+def torch_maid_run(inst, max_upper, dtype, dev, fft=False):
     """The same Algorithm 2 written with PyTorch tensor ops on the GPU (cuDNN
-    depthwise convolutions with circular padding, element-wise ops, host-side
-    control with a device sync per stopping test), the way the method is
-    written without this library.  Same readings as the library: h with 1/2,
-    Huber TV, FISTA with step 1/L_c and the stopping test on ||grad h(y_k)||,
-    CG from zero, z with the sign of Eq. 3.2, psi of Eq. 3.4, the stop rule.
+    depthwise convolutions with circular padding, or with fft=True the
+    convolution theorem through torch.fft (cuFFT) as the library's FFT path
+    does; element-wise ops, host-side control with a device sync per stopping
+    test), the way the method is written without this library.  Same
+    readings as the library: h with 1/2, Huber TV, FISTA with step 1/L_c and
+    the stopping test on ||grad h(y_k)||, CG from zero, z with the sign of
+    Eq. 3.2, psi of Eq. 3.4, the stop rule.
     Returns (wall ms, fused iterations, upper iterations, b, x)."""
     import torch
     import torch.nn.functional as F
@@ -307,7 +376,8 @@ def torch_maid_run(inst, max_upper, dtype, dev):
     C, H, W = inst.shape
     K = inst.K
     r = (K - 1) // 2
-    alpha, gam, beta = 1e-2, 1e-2, 0.3
+    lp = lower_params(inst)
+    alpha, gam, beta = lp["alpha"], lp["reg_param"], lp["beta"]
     y = torch.tensor(inst.y, dtype=dtype, device=dev)[None]
     a = torch.tensor(inst.a, dtype=dtype, device=dev)
 
@@ -315,10 +385,28 @@ def torch_maid_run(inst, max_upper, dtype, dev):
         return F.conv2d(F.pad(x, (r, r, r, r), mode="circular"), w[:, None], groups=C)
 
     def B(b, x):                          # (b * x)[i,j] = sum b[p,q] x[i-p+r, j-q+r]
+        if fft:
+            return torch.fft.irfft2(khat(b) * torch.fft.rfft2(x), s=(H, W))
         return corr(x, torch.flip(b, (1, 2)))
 
     def Bt(b, z):
+        if fft:
+            return torch.fft.irfft2(torch.conj(khat(b)) * torch.fft.rfft2(z), s=(H, W))
         return corr(z, b)
+
+    kcache = {}
+
+    def khat(b):                          # rfft2 of k(u, v) = b[u + r, v + r] placed periodically
+        key = b.data_ptr(), b._version
+        if key not in kcache:
+            kimg = torch.zeros((C, H, W), dtype=dtype, device=dev)
+            ii = (torch.arange(K, device=dev) - r) % H
+            jj = (torch.arange(K, device=dev) - r) % W
+            kimg.index_put_((torch.arange(C, device=dev)[:, None, None], ii[None, :, None], jj[None, None, :]), b,
+                            accumulate=True)
+            kcache.clear()
+            kcache[key] = torch.fft.rfft2(kimg)[None]
+        return kcache[key]
 
     def Dh(x): return torch.roll(x, -1, 3) - x
     def Dv(x): return torch.roll(x, -1, 2) - x
@@ -381,6 +469,12 @@ def torch_maid_run(inst, max_upper, dtype, dev):
 
     def cross(b, x, q):                   # sum_ij x[i-p+r, j-q+r] (Bq)[i,j] + q[...] (Bx - y)[i,j]
         u, v = B(b, q), B(b, x) - y
+        if fft:                           # all lags from F(u) conj F(x) + F(v) conj F(q), read at (p - r, q - r)
+            lag = torch.fft.irfft2(torch.fft.rfft2(u) * torch.conj(torch.fft.rfft2(x)) +
+                                   torch.fft.rfft2(v) * torch.conj(torch.fft.rfft2(q)), s=(H, W))[0]
+            ii = (torch.arange(K, device=dev) - r) % H
+            jj = (torch.arange(K, device=dev) - r) % W
+            return lag[:, ii][:, :, jj]
         xp = F.pad(x, (r, r, r, r), mode="circular")
         qp = F.pad(q, (r, r, r, r), mode="circular")
         s1 = F.conv2d(xp, u[0][:, None], groups=C)        # (1, C, K, K): lag K-1-p, K-1-q
@@ -461,7 +555,7 @@ def run_ours(args):
                                   prec=adp.ADP_F64 if f64 else adp.ADP_F32), y, a)
     if lp["sqrt_tv"]:
         args.no_torch_baseline = True   # the PyTorch MAID baseline implements the Huber TV only
-    fft = args.operator_path == "fft"
+    fft = args.operator_path == "fft" or (args.operator_path == "auto" and spec.get("path") == "fft")
     if fft:
         prob.set_fft(True)
     batch = adp.Batch([prob])
@@ -510,15 +604,30 @@ def run_ours(args):
     for _ in range(3):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        maid_run(prob, a, y)
+        _, hs_iters, hs_passes, _, _, _, _, _ = maid_run(prob, a, y)
         torch.cuda.synchronize()
         hs_ms.append((time.perf_counter() - t0) * 1e3)
+    ll_split, cg_split = maid_run.split
+
+    # the lower-level FISTA iteration alone, event-timed inside the kernel
+    # (launches of n and 2n iterations from the same start: the per-solve
+    # set-up cancels), for its own roofline line
+    ls = {}
+    for n_it in (20, 40, 20, 40):
+        xx = y.clone()
+        prob.lower_solve(a, xx, 0.0, n_it)
+        ls[n_it] = prob.last_kernel_ms()
+    ll_iter_us = (ls[40] - ls[20]) / 20 * 1e3
 
     # the plain host-driven GPU MAID on the same runs (two runs, the first
     # warm), with the direct correlation
+    # (the direct correlation, except on an FFT-path workload, where the host
+    # drives the same FFT-path solves: the direct 63 x 63 correlation at 2048^2
+    # takes about a minute per upper iteration)
     pms, plain_psnr = None, None
+    plain_path = "fft" if fft and spec.get("path") == "fft" else "direct"
     if not args.no_plain:
-        prob.set_fft(False)
+        prob.set_fft(plain_path == "fft")
         plain_maid_run(prob, a, y)
         pms, pups, pb, px = plain_maid_run(prob, a, y)
         pxr = px.double().cpu().numpy()
@@ -528,8 +637,8 @@ def run_ours(args):
     # the same method written with PyTorch tensor ops (one run, after a warm one)
     tms, tfused, tups, tb, tx = 0.0, 0, 0, None, None
     if not args.no_torch_baseline:
-        torch_maid_run(inst, MAX_UPPER, tdt, dev)
-        tms, tfused, tups, tb, tx = torch_maid_run(inst, MAX_UPPER, tdt, dev)
+        torch_maid_run(inst, MAX_UPPER, tdt, dev, fft=fft)
+        tms, tfused, tups, tb, tx = torch_maid_run(inst, MAX_UPPER, tdt, dev, fft=fft)
         torch_psnr = 10 * np.log10(1.0 / np.mean((tx.double().cpu().numpy() - inst.x_true) ** 2))
 
     # end to end through the public API with host buffers: per run, H2D of the
@@ -563,15 +672,29 @@ def run_ours(args):
     flops = passes * 2.0 * K * K * N
     achieved = flops / (kern_ms / 1e3) / 1e12
     traffic = committed_traffic("maid_run_rgb256_k15_traffic.json", MAID_SOURCES) if not fft else None
-    if fft:   # FFT path: bound by memory traffic, FFT_BYTES_PER_VALUE per value and pass
+    if fft:   # FFT path: bound by memory traffic
         hbm = float(pk.get("hbm_gbs", 6787.2))
-        ach_gbs = passes * FFT_BYTES_PER_VALUE * N / (kern_ms / 1e3) / 1e9
+        r2c = prob.fft_pipeline() == 2
+        per_run = hs_passes                 # one host-stepped run: the same program as a graph run
+        if r2c:
+            other = max(per_run - ll_split - cg_split, 0)
+            run_bytes = N * (R2C_FISTA_BYTES * ll_split + R2C_CG_BYTES * cg_split + FFT_BYTES_PER_VALUE * other)
+            basis = (f"{R2C_FISTA_BYTES} B per value and FISTA iteration, {R2C_CG_BYTES} per CG iteration "
+                     f"(real-to-complex pipeline), {FFT_BYTES_PER_VALUE} per other convolution pass (complex "
+                     "pipeline); iteration and pass counts of a host-stepped run of the same program")
+        else:
+            run_bytes = N * FFT_BYTES_PER_VALUE * per_run
+            basis = f"{FFT_BYTES_PER_VALUE} B per value and convolution pass, passes counted on the device"
+        ach_gbs = run_bytes * args.steps / (kern_ms / 1e3) / 1e9
+        ll_gbs = R2C_FISTA_BYTES * N / (ll_iter_us * 1e-6) / 1e9 if r2c else None
         roof = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm, "unit": "GB/s", "frac": ach_gbs / hbm,
-                "traffic": traffic, "kernel": "adp_kernel<float, FFT> (persistent MAID step, graph-replayed)",
+                "traffic": traffic, "kernel": "adp_kernel<float, FFT> (whole MAID run, graph-replayed)",
                 "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "bytes_basis": f"{FFT_BYTES_PER_VALUE} B per value and convolution pass (the FFT pass's "
-                               "row, column and inverse-row phases and its epilogue read), passes counted "
-                               "on the device",
+                "bytes_basis": basis, "fft_pipeline": prob.fft_pipeline(),
+                "fista_iteration": {"us": ll_iter_us, "achieved_gbs": ll_gbs,
+                                    "frac": (ll_gbs / hbm) if ll_gbs else None,
+                                    "basis": f"{R2C_FISTA_BYTES} B per value, event-timed launches of 20 and 40 "
+                                             "iterations"},
                 "direct_equivalent_tflops": achieved}
     else:
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
@@ -592,7 +715,8 @@ def run_ours(args):
                  "form": "device-resident run: one cooperative launch runs all upper iterations (a CUDA graph of one kernel node)",
                  "host_stepped_s": statistics.median(hs_ms) / 1e3,
                  "operator_path": "fft" if fft else "direct",
-                 "plain_gpu_maid_s": pms / 1e3 if pms else None,
+                 "plain_gpu_maid_s": pms / 1e3 if pms else None, "plain_operator_path": plain_path,
+                 "torch_maid_operators": ("torch.fft (cuFFT)" if fft else "cuDNN depthwise conv2d") if tms else None,
                  "speedup_vs_plain": pms / (tot_ms_max / args.steps) if pms else None,
                  "torch_maid_s": (tms / 1e3) if tms else None,
                  "torch_maid_fused_iters": tfused or None, "torch_maid_upper_iters": tups or None,
@@ -616,6 +740,15 @@ def run_ours(args):
                  if spec["cpu_crop"] else f"the {C}x{H}x{W}, K={K} workload")
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{iters_cpu} FISTA iterations of the FP64 oracle on {where} ({dt:.1f} s)"}
+        try:
+            va, np_ = oracle_sample_all_cores(inst, iters_cpu, spec["cpu_crop"])
+            line["cpu_baseline_all_cores"] = {
+                "value": va, "unit": UNIT, "cores": np_, "kind": "oracle",
+                "sample": f"{np_} processes at once, each {iters_cpu} FISTA iterations of the FP64 oracle on "
+                          + (f"its own {spec['cpu_crop']}x{spec['cpu_crop']} crop" if spec["cpu_crop"] else
+                             "the whole image") + "; value = all units / the slowest process's time"}
+        except Exception as e:     # the all-core sample is a reported extra, not the contract's baseline
+            line["cpu_baseline_all_cores"] = {"unavailable": str(e)[:200]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -784,7 +917,8 @@ def run_bf16_operator(args):
 
 def run_profile_case(args):
     """A short fixed program for profiler captures: problem creation, then three
-    lower-level launches of 4 FISTA iterations each (no timing, no JSON)."""
+    lower-level launches of --profile-iters FISTA iterations each (4 by
+    default; no timing, no JSON)."""
     import torch
     from paper_2502_09758_gb300 import adp, synth
     inst = synth.WORKLOADS[args.profile_case](0)
@@ -796,7 +930,7 @@ def run_profile_case(args):
         prob.set_fft(True)
     for _ in range(3):
         x = y.clone()
-        prob.lower_solve(a, x, 0.0, 4)
+        prob.lower_solve(a, x, 0.0, args.profile_iters)
     torch.cuda.synchronize()
     print(f"profile case {args.profile_case}: last launch {prob.last_kernel_ms():.3f} ms")
 
@@ -804,22 +938,24 @@ def run_profile_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--operator-path", default="direct", choices=["direct", "fft"],
-                    help="fft: the MAID runs evaluate B, B^T and A through 2-D FFTs (adp_set_fft)")
+    ap.add_argument("--operator-path", default="auto", choices=["auto", "direct", "fft"],
+                    help="fft: the MAID runs evaluate B, B^T and A through 2-D FFTs (adp_set_fft); "
+                         "auto: the workload's own path (FFT at 2048^2, direct elsewhere)")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the plain host-driven GPU MAID (reported beside the run)")
     ap.add_argument("--no-torch-baseline", action="store_true",
                     help="skip the MAID written with PyTorch tensor ops (reported beside the run)")
-    ap.add_argument("--workload", default="rgb256_k15",
+    ap.add_argument("--workload", default="rgb2048_k63",
                     choices=list(WORKLOAD_SPECS) + ["batch64", "bf16_operator"],
-                    help="rgb256_k15 (default) is the headline line; the others measure the other workloads: "
+                    help="rgb2048_k63 (default) is the headline line; the others measure the other workloads: "
                          "batch64 the 64-problem batch, batched vs one at a time; bf16_operator the "
                          "tensor-core operator against the FP32 one")
+    ap.add_argument("--profile-iters", type=int, default=4)
     ap.add_argument("--profile-case", default=None, choices=["rgb256_k15_motion", "rgb512_k31_gauss_perturbed",
                                                               "rgb2048_k63_motion_gauss"],
                     help="run a short fixed lower-level program for profiler captures")

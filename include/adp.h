@@ -114,11 +114,27 @@ int adp_bf16_grid_size(adp_problem *p);
  * otherwise ADP_EINVAL and the path is unchanged.  The first enable allocates
  * 32 bytes per value, C x H x W x 32 bytes in all (three complex images and two
  * real ones; kept until the problem is destroyed).
- * enable = 0 returns to the direct correlation.  A batch (adp_batch_*) of one
- * problem follows the problem's path; batches of several problems use the
+ * enable = 0 returns to the direct correlation; enable = 2 selects the FFT
+ * path with the complex pipeline only (no real-to-complex pipeline, see
+ * adp_fft_pipeline).  The FFT-path kernel runs 16 warps per CTA with the
+ * problem's grid and all the shared memory a co-resident CTA may have;
+ * ADP_EINVAL when that grid cannot be co-resident.  A batch (adp_batch_*) of
+ * one problem follows the problem's path; batches of several problems use the
  * direct correlation. */
 adp_status adp_set_fft(adp_problem *p, int enable);
 int adp_fft_enabled(adp_problem *p);
+/* Which pipeline carries the FFT path's lower-level solves: 0 the direct
+ * correlation (FFT path off), 1 complex 2-D transforms of the whole image,
+ * 2 the real-to-complex pipeline.  With the FFT path on and W >= 4, when its
+ * staging fits in shared memory, the FISTA iteration of adp_lower_solve (and
+ * of the solves inside adp_maid_step) runs as two grid phases: row transforms
+ * of row pairs packed as one complex row, fused with the gradient, the
+ * updates and the next iterate's forward transform; then the column
+ * transforms of the half spectrum (columns 0 .. W/2) with the symbol
+ * |F(k)|^2 of B^T B, less F(B^T y) (computed once per solve).  The CG of
+ * adp_hypergrad (and of MAID) takes the same path for its Hessian products.
+ * Its extra buffers (about C*H*W*14 bytes) are allocated by adp_set_fft. */
+int adp_fft_pipeline(adp_problem *p);
 
 /* out = grad_x h(x, b) = B^T(B x - y) + alpha grad J(x)   (Prop. 1, gradient);
  * *norm = ||out||_2 accumulated in FP64.  `out` may be NULL. */
@@ -239,6 +255,18 @@ adp_status adp_batch_maid_run_graph(adp_batch *bt, adp_maid_state *st, void *con
 int adp_batch_group_size(adp_batch *bt, int i);
 double adp_batch_last_kernel_ms(adp_batch *bt);
 
+/* Launch shape of p's direct-path kernel (no counterpart in the paper: the
+ * tile-shape knob of a launch-shape autotuner): grid CTAs of nw warps (even,
+ * 2..8).  Strips of 32 x MR pixels are dealt to the grid's warps, so the
+ * shape decides how evenly the strips of a pass spread, and how many warps
+ * share an SM.  ADP_EINVAL when the warps' stages do not fit in shared memory
+ * or the grid cannot be co-resident; the reduction slots grow (cudaMalloc) when
+ * the new shape needs more.  Set it before adp_set_fft and before creating a
+ * batch with p (both take the problem's shape then).  The problem's initial
+ * shape is one CTA per SM of the most warps that fit, or enough CTAs for a
+ * strip per warp. */
+adp_status adp_set_launch(adp_problem *p, int grid, int nw);
+
 /* Diagnostics of the last call on p: number of full-image convolution passes
  * it executed (each is 2 K^2 C H W flops; the kernel-gradient correlation
  * counts as two), and the number of CTAs of its cooperative launch. */
@@ -274,7 +302,10 @@ double adp_last_kernel_ms(adp_problem *p);
  * ADP_NOALLOC_WEIGHT_BYTES; larger problems are rejected with ADP_EINVAL.
  * The first call on a device looks up the array's device address and sets
  * kernel attributes for that device (once per device, with it current); make
- * that first call before any stream capture.  All calls share the array and
+ * that first call before any stream capture.  Every call waits for its
+ * stream to finish the solve and reads the iteration count and gradient norm
+ * back to the host before it returns.  The device used is the current one:
+ * the pointers and the stream must belong to it.  All calls share the array and
  * it keeps the last call's contents (each call clears what must start at
  * zero), so calls whose GPU work overlaps -- on different streams, or from
  * different threads -- race and must be serialised by the caller.  Calls no

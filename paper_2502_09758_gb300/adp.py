@@ -27,7 +27,7 @@ ADP_REG_HUBER_TV, ADP_REG_SQRT_TV, ADP_REG_QUAD = 0, 1, 2
 # every entry point declared in include/adp.h
 EXPORTS = ("adp_problem_create", "adp_problem_destroy", "adp_apply_B", "adp_apply_Bt",
            "adp_apply_B_bf16", "adp_apply_Bt_bf16", "adp_bf16_prep_ms_last", "adp_bf16_grid_size",
-           "adp_set_fft", "adp_fft_enabled",
+           "adp_set_fft", "adp_fft_enabled", "adp_fft_pipeline", "adp_set_launch",
            "adp_grad_lower", "adp_hess_vec", "adp_lower_solve", "adp_upper_loss", "adp_hypergrad",
            "adp_cross_t", "adp_maid_init", "adp_maid_step", "adp_conv_passes_last",
            "adp_grid_size", "adp_warps_per_cta", "adp_last_kernel_ms", "adp_trace_enable",
@@ -87,6 +87,8 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
             "adp_bf16_grid_size": (i, [P]),
             "adp_set_fft": (i, [P, i]),
             "adp_fft_enabled": (i, [P]),
+            "adp_fft_pipeline": (i, [P]),
+            "adp_set_launch": (i, [P, i, i]),
             "adp_grad_lower": (i, [P, vp, vp, vp, dp]),
             "adp_hess_vec": (i, [P, vp, vp, vp, vp]),
             "adp_lower_solve": (i, [P, vp, vp, d, i, ip, dp]),
@@ -242,12 +244,21 @@ class Problem:
         _check(self.lib.adp_apply_Bt_bf16(self.handle, self._k(b, "b"), self._i(z, "z"), self._i(out, "out")))
         return out
 
-    def set_fft(self, enable=True):
-        """Evaluate the operators of later calls through 2-D FFTs (FP32, power-of-two H, W)."""
-        _check(self.lib.adp_set_fft(self.handle, 1 if enable else 0))
+    def set_fft(self, enable=True, complex_only=False):
+        """Evaluate the operators of later calls through 2-D FFTs (FP32, power-of-two H, W);
+        complex_only keeps the lower solves and CG off the real-to-complex pipeline."""
+        _check(self.lib.adp_set_fft(self.handle, (2 if complex_only else 1) if enable else 0))
 
     def fft_enabled(self) -> bool:
         return bool(self.lib.adp_fft_enabled(self.handle))
+
+    def set_launch(self, grid, nw):
+        """Launch shape of the direct-path kernel: grid CTAs of nw warps."""
+        _check(self.lib.adp_set_launch(self.handle, int(grid), int(nw)))
+
+    def fft_pipeline(self) -> int:
+        """0: direct correlation; 1: complex FFT pipeline; 2: real-to-complex lower solves."""
+        return int(self.lib.adp_fft_pipeline(self.handle))
 
     def bf16_prep_ms(self) -> float:
         return float(self.lib.adp_bf16_prep_ms_last(self.handle))
@@ -369,13 +380,18 @@ def adp_lower_solve_noalloc(params: Params, y, b, x, eps, max_iters=300, stream=
     need the solve.  In place on x; returns (updates, ||grad_x h||, capped)."""
     lib = load_library()
     img, ker = (params.C, params.H, params.W), (params.C, params.K, params.K)
-    s = stream if stream is not None else torch.cuda.current_stream(x.device)
+    for name, t in (("y", y), ("b", b)):
+        if isinstance(t, torch.Tensor) and t.device != x.device:
+            raise ValueError(f"{name} must be on {x.device}, got {t.device}")
     it, gn = ct.c_int(), ct.c_double()
     cp = params.c()
-    st = _check(lib.adp_lower_solve_noalloc(ct.byref(cp), _ptr(y, img, params.dtype, "y"),
-                                            _ptr(b, ker, params.dtype, "b"), _ptr(x, img, params.dtype, "x"),
-                                            float(eps), int(max_iters), ct.c_void_p(s.cuda_stream),
-                                            ct.byref(it), ct.byref(gn)), ok=(ADP_OK, ADP_ENOCONV))
+    # the library resolves its array and device limits for the current device
+    with torch.cuda.device(x.device):
+        s = stream if stream is not None else torch.cuda.current_stream(x.device)
+        st = _check(lib.adp_lower_solve_noalloc(ct.byref(cp), _ptr(y, img, params.dtype, "y"),
+                                                _ptr(b, ker, params.dtype, "b"), _ptr(x, img, params.dtype, "x"),
+                                                float(eps), int(max_iters), ct.c_void_p(s.cuda_stream),
+                                                ct.byref(it), ct.byref(gn)), ok=(ADP_OK, ADP_ENOCONV))
     return it.value, gn.value, st == ADP_ENOCONV
 
 

@@ -69,6 +69,11 @@ struct adp_problem {
     cudaStream_t stream;
     int device, grid, nw;  // CTAs of the cooperative launch, warps per CTA
     size_t smem;           // dynamic shared memory per CTA (bytes)
+    size_t smem_fft;       // the same for the FFT-path kernel (adp_set_fft)
+    int nw_fft;            // warps per CTA of the FFT-path kernel
+    int grid_fft;          // CTAs of its cooperative launch
+    int part_cap;          // CTAs the reduction slots (part) hold
+    size_t zpart_cap;      // warps the per-warp kernel-gradient rows (zpart) hold
     size_t esize;
     Geom g;                // padded layout and strips
     void *ws;              // NBUF padded images
@@ -90,6 +95,12 @@ struct adp_problem {
     int fft, flogH, flogW, fcb, frb;
     float2 *fz, *fs, *fy, *ftw;  // complex scratch, kernel spectrum, second spectrum, twiddles (H/2, W/2)
     float *fout, *fc;       // correlation of the last FFT pass; B^T y of the current lower solve
+    // real-to-complex pipeline of the FFT-path lower solve (fr2c = 0: not used)
+    int fr2c, frp, fcb2, fpsh, fnst, fncs, fstage, fcstage, frows;
+    float2 *fzh, *fzn;      // half spectra (C x H x W/2) and the column W/2 (C x H)
+    float *fsh, *fsn;       // |F(k)|^2 at those columns
+    float2 *fkh, *fkn;      // F(k) at those columns
+    float2 *fch, *fcn;      // F(B^T y_delta) of the current lower solve
 };
 
 // ------------------------------------------------------------ tensor maps
@@ -189,6 +200,10 @@ static Ctx<T> make_ctx(const adp_problem *p)
         c.fft = 1; c.flogH = p->flogH; c.flogW = p->flogW; c.fcb = p->fcb; c.frb = p->frb;
         c.fz = p->fz; c.fs = p->fs; c.fy = p->fy; c.fout = (T *)p->fout; c.fc = (T *)p->fc;
         c.ftwH = p->ftw; c.ftwW = p->ftw + q.H / 2;
+        c.fr2c = p->fr2c; c.frp = p->frp; c.fcb2 = p->fcb2; c.fpsh = p->fpsh; c.fnst = p->fnst;
+        c.fstage = p->fstage; c.fcstage = p->fcstage; c.frows = p->frows; c.fncs = p->fncs;
+        c.fzh = p->fzh; c.fzn = p->fzn; c.fsh = p->fsh; c.fsn = p->fsn;
+        c.fkh = p->fkh; c.fkn = p->fkn; c.fch = p->fch; c.fcn = p->fcn;
     }
     return c;
 }
@@ -203,7 +218,9 @@ static adp_status launch(adp_problem *p, Job<T> &jb)
     void *args[] = {(void *)&cx, (void *)&jb};
     const void *fn = std::is_same<T, float>::value ? (p->fft ? kernel_f32_fft() : kernel_f32()) : kernel_f64();
     CK(cudaEventRecord(p->ev0, p->stream));
-    CK(cudaLaunchCooperativeKernel(fn, dim3(p->grid), dim3(32 * p->nw), args, p->smem, p->stream));
+    const bool fftk = std::is_same<T, float>::value && p->fft;
+    CK(cudaLaunchCooperativeKernel(fn, dim3(fftk ? p->grid_fft : p->grid), dim3(32 * (fftk ? p->nw_fft : p->nw)),
+                                   args, fftk ? p->smem_fft : p->smem, p->stream));
     CK(cudaEventRecord(p->ev1, p->stream));
     CK(cudaMemcpyAsync(p->hout, p->dout, sizeof(DevOut), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
@@ -266,7 +283,8 @@ void adp_problem_destroy(adp_problem *p)
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
     tc_plan_destroy(p->tc);
-    void *fptrs[] = {p->fz, p->fs, p->fy, p->ftw, p->fout, p->fc};
+    void *fptrs[] = {p->fz, p->fs, p->fy, p->ftw, p->fout, p->fc, p->fzh, p->fzn, p->fsh, p->fsn,
+                     p->fkh, p->fkn, p->fch, p->fcn};
     for (void *q : fptrs) if (q) cudaFree(q);
     free(p->a_host);
     free(p);
@@ -360,7 +378,9 @@ adp_status adp_problem_create(const adp_params *prm, const void *y, const void *
     CKC(cudaMalloc(&p->BT, KK * p->esize));
     CKC(cudaMalloc(&p->ZK, KK * p->esize));
     CKC(cudaMalloc((void **)&p->part, (size_t)NSLOT * p->grid * sizeof(double)));
+    p->part_cap = p->grid;
     CKC(cudaMalloc((void **)&p->zpart, (size_t)p->grid * p->nw * KK * sizeof(double)));
+    p->zpart_cap = (size_t)p->grid * p->nw;
     CKC(cudaMalloc((void **)&p->bar, sizeof(unsigned)));
     CKC(cudaMalloc((void **)&p->dout, sizeof(DevOut)));
     CKC(cudaMallocHost((void **)&p->hout, sizeof(DevOut)));
@@ -477,33 +497,56 @@ adp_status adp_set_fft(adp_problem *p, int enable)
     const int lh = log2_exact(q.H), lw = log2_exact(q.W);
     if (lh < 1 || lw < 1 || q.H > 8192 || q.W > 8192)
         return set_err(ADP_EINVAL, "FFT path needs H and W powers of two in 2..8192%s", "", 0);
-    // shared scratch of the FFT phases: the warp regions of a CTA
+    // the FFT-path kernel: FFT_WARPS warps per CTA, whose warp regions hold
+    // only the epilogue tiles, up to FFT_CTAS_PER_SM CTAs per SM (so that
+    // independent tasks overlap one another's latency): a grid of that many
+    // CTAs per SM when the problem's own grid fills the SMs, else the
+    // problem's grid; all the dynamic shared memory a co-resident CTA may have
+    // (less the weights) is the scratch of the FFT phases
     const size_t esz = sizeof(float);
-    const Layout<float> L(q.C, q.K, p->nw, p->g.wsm);
-    const size_t scratch = (size_t)p->nw * L.warp_elems * esz;
+    const int nwf = FFT_WARPS;
+    const Layout<float> L(q.C, q.K, nwf, p->g.wsm, true);
+    CK(cudaSetDevice(p->device));
+    size_t smem_fft = 0;
+    int grid_fft = p->grid;
+    {
+        int nsm = 0, maxsmem = 0, occ = 0;
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
+        CK(cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+        CK(optin_dynamic_smem(kernel_f32_fft(), maxsmem));
+        cudaFuncAttributes fa;
+        CK(cudaFuncGetAttributes(&fa, kernel_f32_fft()));
+        if (p->grid >= nsm) grid_fft = std::min(FFT_CTAS_PER_SM * nsm, GT_MAX);
+        // the largest shared memory at which that grid stays co-resident
+        for (size_t cand = (size_t)maxsmem - fa.sharedSizeBytes; cand >= (size_t)L.total * esz; cand -= 4096) {
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel_f32_fft(), 32 * nwf, cand));
+            if ((long long)occ * nsm >= grid_fft) { smem_fft = cand; break; }
+            if (cand < 4096 + (size_t)L.total * esz) break;
+        }
+        if (!smem_fft)
+            return set_err(ADP_EINVAL, "FFT path: kernel not co-resident at its grid%s (%lld CTAs)", "", grid_fft);
+    }
+    if (grid_fft > p->part_cap) {      // reduction slots for the larger grid (kept once grown)
+        double *np_ = nullptr;
+        CK(cudaMalloc((void **)&np_, (size_t)NSLOT * grid_fft * sizeof(double)));
+        CK(cudaFree(p->part));
+        p->part = np_;
+        p->part_cap = grid_fft;
+    }
+    const size_t scratch = smem_fft - (size_t)L.w_elems * esz;
     if ((size_t)q.W * 8 > scratch)
         return set_err(ADP_EINVAL, "FFT path: image rows too long for shared memory%s (W = %lld)", "", q.W);
     // columns per column block and rows per row batch: powers of two, at most
     // 32, within the scratch, and small enough that every CTA gets a block
     auto pick = [&](int len, int count_total, int limit) {
         int v = 32;
-        while (v > 1 && ((size_t)len * v * 8 > scratch || v > limit || (long long)count_total / v < p->grid)) v >>= 1;
+        while (v > 1 && ((size_t)len * v * 8 > scratch || v > limit || (long long)count_total / v < grid_fft)) v >>= 1;
         return v;
     };
     const int cb = pick(q.H, q.C * q.W, q.W), rb = pick(q.W, q.C * q.H, q.H);
     if ((size_t)q.H * cb * 8 > scratch)
         return set_err(ADP_EINVAL, "FFT path: image columns too long for shared memory%s (H = %lld)", "", q.H);
-    CK(cudaSetDevice(p->device));
-    {   // the FFT instantiation must be co-resident at the problem's grid
-        int nsm = 0, maxsmem = 0, occ = 0;
-        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
-        CK(cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
-        CK(optin_dynamic_smem(kernel_f32_fft(), maxsmem));
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel_f32_fft(), 32 * p->nw, p->smem));
-        if ((long long)occ * nsm < p->grid)
-            return set_err(ADP_EINVAL, "FFT path: kernel not co-resident at the problem's grid%s (%lld CTAs)", "",
-                           p->grid);
-    }
+    const size_t scratch_r2c = scratch;
     if (!p->fz) {
         const size_t n = (size_t)q.C * q.H * q.W;
         CK(cudaMalloc((void **)&p->fz, n * sizeof(float2)));
@@ -525,11 +568,119 @@ adp_status adp_set_fft(adp_problem *p, int enable)
     p->flogW = lw;
     p->fcb = cb;
     p->frb = rb;
+    p->smem_fft = smem_fft;
+    p->nw_fft = nwf;
+    p->grid_fft = grid_fft;
+    // the real-to-complex pipeline of the lower solve: row tasks of frp row
+    // pairs (a radix-8 group for each thread where the image allows, and no
+    // fewer tasks than CTAs), column tasks of fcb2 half-spectrum columns, double
+    // buffered when both fit in the scratch (else single), padding of the
+    // row transforms' slots against the bit-reversed reads; W >= 4 so that
+    // every staged row is whole 16-byte copies
+    p->fr2c = 0;
+    if (q.W >= 4 && enable != 2) {
+        // shared memory of a row task with rp row pairs: its half spectra
+        // double buffered (2 rp rows of W/2 + 2 (W/64) float2 each), one buffer
+        // of 4 rp + 4 image rows, the work area; of a column task: two stages
+        const size_t spp = (size_t)(q.W / 2) + 2 * (size_t)(q.W / 64);
+        const int W2 = q.W / 2;
+        int best_rp = 0, cb2 = 0, nst = 0, ncs = 0;
+        size_t st_spc = 0, st_rows = 0;
+        int ps = 31;
+        for (int ns = 2; ns >= 1 && !best_rp; --ns)
+            for (int rp = 1; rp <= q.H / 2; rp *= 2) {
+                // no fewer tasks than CTAs, no more radix-8 groups than threads
+                if (rp > 1 && ((long long)q.C * q.H / (2 * rp) < grid_fft || rp * q.W > 8 * 32 * nwf)) break;
+                int lrp = 0;
+                while ((1 << lrp) < rp) ++lrp;
+                const int psr = lw + lrp >= 9 ? lw + lrp - 5 : 31;
+                const size_t spc = 4 * (size_t)rp * spp, rows = (size_t)(4 * rp + 4) * q.W;     // floats
+                const size_t work = ((size_t)rp * q.W + (((size_t)rp * q.W) >> psr) + 1) * 8;  // bytes
+                if ((ns * spc + rows) * 4 + work > scratch) break;
+                best_rp = rp;
+                nst = ns;
+                st_spc = spc;
+                st_rows = rows;
+                ps = psr;
+            }
+        for (int ns = 2; ns >= 1 && best_rp && !cb2; --ns)
+            for (int c2 = W2 < 16 ? W2 : 16; c2 >= 2; c2 >>= 1) {
+                if ((size_t)ns * q.H * c2 * 8 > scratch) continue;
+                if (c2 > 2 && (long long)q.C * (W2 / c2) < grid_fft) continue;
+                cb2 = c2;
+                ncs = ns;
+                break;
+            }
+        if (best_rp && cb2) {
+            p->frp = best_rp;
+            p->fpsh = ps;
+            p->fnst = nst;
+            p->fncs = ncs;
+            p->fstage = (int)st_spc;
+            p->frows = (int)st_rows;
+            p->fcstage = q.H * cb2;
+            p->fcb2 = cb2;
+            if (!p->fzh) {
+                const size_t nh = (size_t)q.C * q.H * W2, nn = (size_t)q.C * q.H;
+                CK(cudaMalloc((void **)&p->fzh, nh * sizeof(float2)));
+                CK(cudaMalloc((void **)&p->fzn, nn * sizeof(float2)));
+                CK(cudaMalloc((void **)&p->fsh, nh * sizeof(float)));
+                CK(cudaMalloc((void **)&p->fsn, nn * sizeof(float)));
+                CK(cudaMalloc((void **)&p->fkh, nh * sizeof(float2)));
+                CK(cudaMalloc((void **)&p->fkn, nn * sizeof(float2)));
+                CK(cudaMalloc((void **)&p->fch, nh * sizeof(float2)));
+                CK(cudaMalloc((void **)&p->fcn, nn * sizeof(float2)));
+            }
+            p->fr2c = 1;
+        }
+    }
     p->fft = 1;
     return ADP_OK;
 }
 
 int adp_fft_enabled(adp_problem *p) { return p ? p->fft : 0; }
+
+adp_status adp_set_launch(adp_problem *p, int grid, int nw)
+{
+    if (!p) return set_err(ADP_EINVAL, "null problem%s", "", 0);
+    const adp_params &q = p->prm;
+    const Geom &g = p->g;
+    if (nw < 2 || nw > MAXNW || (nw & 1)) return set_err(ADP_EINVAL, "warps per CTA must be even, 2..%s%lld", "", MAXNW);
+    if (grid < 1 || grid > GT_MAX) return set_err(ADP_EINVAL, "grid must be 1..%s%lld CTAs", "", GT_MAX);
+    CK(cudaSetDevice(p->device));
+    int nsm = 0, maxsmem = 0, occ = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
+    CK(cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    const int total = q.prec == ADP_F32 ? Layout<float>(q.C, q.K, nw, g.wsm).total : Layout<double>(q.C, q.K, nw, g.wsm).total;
+    const size_t smem = (size_t)total * p->esize;
+    if (smem + SMEM_STATIC_MARGIN > (size_t)maxsmem)
+        return set_err(ADP_EINVAL, "launch shape: warps' stages exceed shared memory%s (%lld warps)", "", nw);
+    const void *kfn = q.prec == ADP_F32 ? kernel_f32() : kernel_f64();
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, 32 * nw, smem));
+    if ((long long)occ * nsm < grid)
+        return set_err(ADP_EINVAL, "launch shape: grid not co-resident%s (%lld CTAs)", "", grid);
+    const size_t KK = (size_t)q.C * q.K * q.K;
+    if (grid > p->part_cap) {
+        double *np_ = nullptr;
+        CK(cudaMalloc((void **)&np_, (size_t)NSLOT * grid * sizeof(double)));
+        CK(cudaFree(p->part));
+        p->part = np_;
+        p->part_cap = grid;
+    }
+    if ((size_t)grid * nw > p->zpart_cap) {
+        double *nz = nullptr;
+        CK(cudaMalloc((void **)&nz, (size_t)grid * nw * KK * sizeof(double)));
+        CK(cudaFree(p->zpart));
+        p->zpart = nz;
+        p->zpart_cap = (size_t)grid * nw;
+    }
+    p->grid = grid;
+    p->nw = nw;
+    p->smem = smem;
+    return ADP_OK;
+}
+
+int adp_fft_pipeline(adp_problem *p) { return !p || !p->fft ? 0 : (p->fr2c ? 2 : 1); }
 
 double adp_bf16_prep_ms_last(adp_problem *p) { return p && p->tc ? (double)p->tc_times.prep_ms : -1.0; }
 int adp_bf16_grid_size(adp_problem *p) { return p ? tc_grid(p->tc) : 0; }
@@ -853,9 +1004,10 @@ static adp_status batch_launch(adp_batch *bt, cudaStream_t stream)
     void **args = one ? args_one : args_many;
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof cfg);
-    cfg.gridDim = dim3((unsigned)bt->first[n]);
-    cfg.blockDim = dim3(32 * bt->nw);
-    cfg.dynamicSmemBytes = bt->smem;
+    const bool fftk = one && bt->prec == ADP_F32 && bt->ps[0]->fft;
+    cfg.gridDim = dim3((unsigned)(fftk ? bt->ps[0]->grid_fft : bt->first[n]));
+    cfg.blockDim = dim3(32 * (fftk ? bt->ps[0]->nw_fft : bt->nw));
+    cfg.dynamicSmemBytes = fftk ? bt->ps[0]->smem_fft : bt->smem;
     cfg.stream = stream;
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeCooperative;

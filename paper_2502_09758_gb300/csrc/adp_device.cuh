@@ -10,7 +10,10 @@
 
 namespace adp {
 
-constexpr int MAXNW = 8;           // most warps per CTA
+constexpr int MAXNW = 8;           // most warps per CTA (direct correlation)
+constexpr int MAXNW_FFT = 16;      // warps per CTA the static arrays allow
+constexpr int FFT_WARPS = 16;      // warps per CTA of the FFT-path kernel
+constexpr int FFT_CTAS_PER_SM = 1; // its CTAs per SM
 constexpr int MAXC = 64;           // channels supported (per-channel step cache)
 constexpr int KMAX = 63;           // largest odd kernel size supported
 constexpr int NSLOT = 8;           // scalar reduction slots
@@ -286,6 +289,18 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
 }
 
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// wait until at most n of this thread's most recent cp.async groups are pending
+template <int n>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(n) : "memory"); }
+
 // warp 0 only; entries are 8-byte scalars
 template <typename T>
 __device__ __forceinline__ void grid_issue(const typename Scal<T>::S *part, int n, typename Scal<T>::S *sbuf)
@@ -546,6 +561,19 @@ struct Ctx {
     T *fout;                           // the correlation of the last FFT pass, dense C x H x W
     T *fc;                             // B^T y_delta of the current lower solve (FFT path), dense
     const float2 *ftwH, *ftwW;         // twiddles exp(-2 pi i j / n), j < n/2, for n = H and n = W
+    // real-to-complex pipeline of the FFT-path FISTA iteration (fr2c = 0: the
+    // complex pipeline above carries it)
+    int fr2c;                          // 1: lower solves use the real-to-complex pipeline
+    int frp;                           // row pairs per row task
+    int fcb2;                          // half-spectrum columns per column task
+    int fpsh;                          // padding shift of the row tasks' transform slots
+    int fnst, fstage, fcstage;         // half-spectrum row stages (1 or 2); floats per row stage; float2 per column stage
+    int fncs;                          // column stages (1 or 2)
+    int frows;                         // floats of the row tasks' image-row buffer
+    float2 *fzh, *fzn;                 // half spectra C x H x W/2 (columns 0 .. W/2-1) and the column W/2, C x H
+    float *fsh, *fsn;                  // |F(k)|^2 at those columns: tiled per column task, and at W/2
+    float2 *fkh, *fkn;                 // F(k) itself, same layout
+    float2 *fch, *fcn;                 // F(B^T y_delta) of the current lower solve, same layout
 };
 
 template <typename T>
@@ -574,7 +602,7 @@ struct Job {
 template <typename T>
 struct Layout {
     int r, r4, Kp, BW, NX, stage, tile1, tileI, w_elems, warp_elems, total;
-    __host__ __device__ Layout(int C, int K, int nw, int wsm)
+    __host__ __device__ Layout(int C, int K, int nw, int wsm, bool fft = false)
     {
         constexpr int MR = Cfg<T>::MR, PC = Cfg<T>::PC;
         r = (K - 1) / 2;
@@ -582,7 +610,7 @@ struct Layout {
         Kp = round_up(K, PC);
         BW = round_up(32 + r + r4, 4);
         NX = PC + MR - 1;
-        stage = round_up(NX * BW, 32);
+        stage = fft ? 0 : round_up(NX * BW, 32);   // the FFT-path kernel has no correlation stages
         tile1 = round_up((MR + 2) * 40, 32);
         tileI = round_up(MR * 32, 32);
         w_elems = wsm ? round_up(2 * C * Kp * K, 32) : 0;

@@ -41,15 +41,15 @@ namespace adp {
 // CTA-wide scratch of the engine in static shared memory (namespace scope, so
 // that its addresses are constants rather than values held in registers).
 // The reduction scalar S is 8 bytes (a float-float pair or a double).
-__shared__ __align__(16) double g_red[MAXNW];
+__shared__ __align__(16) double g_red[MAXNW_FFT];
 __shared__ __align__(16) double g_bcast[2];
-__shared__ double g_redd[MAXNW];
+__shared__ double g_redd[MAXNW_FFT];
 __shared__ __align__(16) double g_tau[MAXC];
 __shared__ __align__(16) double g_gbuf[GT_MAX];
 __shared__ int g_sflag;
 // each warp's two mbarriers (outside the warp regions, which the FFT phases
 // reuse as one CTA-wide scratch area between passes)
-__shared__ __align__(8) uint64_t g_mbar[MAXNW][2];
+__shared__ __align__(8) uint64_t g_mbar[MAXNW_FFT][2];
 
 // Report of a MAID step, accumulated by thread 0 of each CTA (shared memory,
 // so that it occupies no registers while the solves run).
@@ -59,6 +59,10 @@ struct MaidRep {
     double loss, gxn, znorm, psi;
 };
 __shared__ MaidRep g_rep;
+// channel sums and means of the FFT kernel-gradient correlation (MAXC channels)
+__shared__ double g_csum[4 * MAXC];
+__shared__ double g_mx[MAXC], g_mv[MAXC];
+__shared__ double g_xoff[MAXC];
 
 // FFTP: compile the FFT operator path in (a separate instantiation, so that
 // the direct program's register allocation does not carry it).
@@ -89,7 +93,8 @@ struct Eng {
     // tiles, an interior tile, the mbarriers)
     static constexpr int TILE1 = round_up((MR + 2) * 40, 32);
     static constexpr int TILEI = round_up(MR * 32, 32);
-    __device__ int stage_elems() const { return round_up(NX * cx.BW, 32); }
+    // (the FFT instantiation has no direct correlation: no stages)
+    __device__ int stage_elems() const { return kFFT ? 0 : round_up(NX * cx.BW, 32); }
     __device__ T *sb1() const { return sb0 + stage_elems(); }
     __device__ T *t1() const { return sb0 + 2 * stage_elems(); }
     __device__ T *t2() const { return t1() + TILE1; }
@@ -114,7 +119,7 @@ struct Eng {
     {
         lane = threadIdx.x & 31;
         warp = threadIdx.x >> 5;
-        const Layout<T> L(cx.C, cx.K, nw(), cx.wsm);
+        const Layout<T> L(cx.C, cx.K, nw(), cx.wsm, kFFT);
         T *base = reinterpret_cast<T *>(smem);   // 128-byte aligned (checked by the kernel)
         wF = wT = nullptr;
         wsm = base;
@@ -281,9 +286,7 @@ struct Eng {
         wT = Tt;
         if (cx.wsm) __syncthreads();
         else sync();
-        if constexpr (kFFT) {
-            if (cx.fft) spectrum(b);
-        }
+        if constexpr (kFFT) spectrum(b);
     }
 
     __device__ S *partS(int slot) const { return reinterpret_cast<S *>(cx.part) + slot * nblk; }
@@ -381,6 +384,9 @@ struct Eng {
                 });
             if (!sync()) return false;
             fft_columns(FM_B, CM_STORE, cx.fs);
+            if (!cx.fr2c) return sync();
+            if (!sync()) return false;
+            gram_symbol();
             return sync();
         } else {
             return false;
@@ -462,16 +468,48 @@ struct Eng {
         }
     }
 
-    // forward row transforms of padded buffer img into cx.fz
-    __device__ void fft_rows_img(int img)
+    // forward row transforms of padded buffer img into cx.fz (less the
+    // per-channel offset off[c] when off is given)
+    __device__ void fft_rows_img(int img, const double *off = nullptr)
     {
         const T *src = buf(img);
         const long long HWp = cx.HWp;
         const int Wp = cx.Wp, Gy = cx.Gy, Gx = cx.Gx;
         for (int r0 = bid * cx.frb; r0 < cx.C * cx.H; r0 += nblk * cx.frb)
             fft_rows_fwd(r0, [=](int c, int i, int j) {
-                return (float)__ldcg(src + c * HWp + (long long)(i + Gy) * Wp + Gx + j);
+                const float v = (float)__ldcg(src + c * HWp + (long long)(i + Gy) * Wp + Gx + j);
+                return off ? (float)((double)v - off[c]) : v;
             });
+    }
+
+    // per-channel sums of the image pixels of buffers b[0..3] into
+    // out[4 c + k] (every CTA obtains the same values: per-CTA partials in
+    // FP64, then a fixed-order total); needs 4 C doubles at out and
+    // nblk x 4 C doubles of cx.zpart.  Ends with a grid barrier.
+    __device__ bool chan_sums(const int (&b)[4], double *out)
+    {
+        const int C = cx.C, W = cx.W;
+        double *part = cx.zpart;
+        for (int c = 0; c < C; ++c) {
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int i = bid; i < cx.H; i += nblk)                  // rows dealt to CTAs
+                for (int j = tid(); j < W; j += blockDim.x)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) acc[k] += (double)__ldcg(buf(b[k]) + pidx(c, i, j));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const double sk = block_sum_d(acc[k], g_redd);
+                if (tid() == 0) part[(long long)bid * 4 * C + 4 * c + k] = sk;
+            }
+        }
+        if (!sync()) return false;
+        for (int e = tid(); e < 4 * C; e += blockDim.x) {
+            double t = 0.0;
+            for (int q = 0; q < nblk; ++q) t += __ldcg(part + (long long)q * 4 * C + e);
+            out[e] = t;
+        }
+        __syncthreads();
+        return true;
     }
 
     // inverse row transforms of cx.fz, real part / (H W) into out (dense)
@@ -514,6 +552,13 @@ struct Eng {
     // V = B x - y in their buffers, out[c, p, q] = sum_n U[n] x[n - d] +
     // V[n] v[n - d] at the lag d = (p - r, q - r) is the inverse transform of
     // F(U) conj(F(x)) + F(V) conj(F(v)), read at d (mod H, W).  Into cx.fout.
+    //
+    // x and v enter the transforms less their channel means m_x, m_v (the
+    // products' zero-frequency terms then vanish, and with them the largest
+    // source of rounding spread over every lag); the means come back as
+    // m_x sum U + m_v sum V, added exactly to every lag of the channel:
+    // cross_off()[c] after the call.
+    __device__ double *cross_off() const { return g_xoff; }
     __device__ bool fft_cross(int bx, int bv)
     {
         if constexpr (kFFT) {
@@ -521,8 +566,17 @@ struct Eng {
             const int modes[4] = {CM_STORE, CM_XSTORE, CM_STORE, CM_XADD};
             float2 *dsts[4] = {cx.fs, cx.fs, cx.fy, cx.fs};
             const float2 *srcs[4] = {nullptr, cx.fs, nullptr, cx.fy};
+            const int sb[4] = {B_U, bx, B_V, bv};
+            if (!chan_sums(sb, g_csum)) return false;
+            const double n = (double)cx.HW;
+            for (int c = tid(); c < cx.C; c += blockDim.x) {
+                g_mx[c] = g_csum[4 * c + 1] / n;
+                g_mv[c] = g_csum[4 * c + 3] / n;
+                g_xoff[c] = g_mx[c] * g_csum[4 * c] + g_mv[c] * g_csum[4 * c + 2];
+            }
+            __syncthreads();
             for (int k = 0; k < 4; ++k) {
-                fft_rows_img(steps[k]);
+                fft_rows_img(steps[k], k == 1 ? g_mx : (k == 3 ? g_mv : nullptr));
                 if (!sync()) return false;
                 fft_columns(FM_B, modes[k], dsts[k], srcs[k]);
                 if (!sync()) return false;
@@ -534,6 +588,486 @@ struct Eng {
         } else {
             return false;
         }
+    }
+
+    // ------------------------------------------------ FFT path, real-to-complex pipeline
+    // The FISTA iteration of the lower solve in two grid phases instead of the
+    // complex pipeline's four.  The image is real, so its 2-D DFT is kept for
+    // the column frequencies nu = 0 .. W/2 only: fzh[c][i][nu] (nu < W/2) and
+    // fzn[c][i] (nu = W/2) hold the row DFTs X_i[nu] of the rows i in natural
+    // order.
+    //   row phase:    rows 2m and 2m+1 of a channel are transformed together
+    //                 as z = u_2m + i u_2m+1; Hermitian symmetry separates
+    //                 them, X_2m[nu] = (Z[nu] + conj Z[-nu]) / 2 and
+    //                 X_2m+1[nu] = (Z[nu] - conj Z[-nu]) / (2i), and packs them
+    //                 back for the inverse.  In the FISTA mode the inverse row
+    //                 transform of (B^T B y_k)'s half spectra, the gradient
+    //                 G = B^T B y_k - B^T y_delta + alpha grad J(y_k), the
+    //                 updates x_{k+1}, y_{k+1} and the forward row transform of
+    //                 y_{k+1} happen in one pass over the rows.
+    //   column phase: per block of fcb2 half-spectrum columns, the forward
+    //                 column transform, the product with |F(k)|^2 (the symbol
+    //                 of B^T B, real), the inverse column transform.
+    // Operands are staged into shared memory with cp.async (16-byte copies)
+    // in fnst buffers, so that the next task's loads run under the current
+    // task's transforms.
+    enum { RF_FWD = 0, RF_FISTA = 1, RF_CGP = 2, RF_HESS = 3 };
+
+    // row phase: fnst half-spectrum stages, the image-row buffer, the work area
+    __device__ float *rstage(int k) const { return reinterpret_cast<float *>(fft_scratch()) + k * cx.fstage; }
+    __device__ float *rrows() const { return rstage(cx.fnst); }
+    __device__ float2 *rwork() const { return reinterpret_cast<float2 *>(rrows() + cx.frows); }
+    // column phase: two stages
+    __device__ float2 *cstage(int k) const { return fft_scratch() + k * cx.fcstage; }
+
+    // |F(k)|^2 and F(k) at the half-spectrum columns from the complex spectrum
+    // cx.fs (bit-reversed along both axes): fsh / fkh[((c*nb + blk)*H + mu)*fcb2 + k]
+    // at column nu = blk*fcb2 + k, fsn / fkn[c*H + mu] at nu = W/2 (bit-reversed
+    // row position mu, the order of the column phase's forward transform)
+    __device__ void gram_symbol()
+    {
+        const int H = cx.H, W = cx.W, W2 = W / 2, CB = cx.fcb2, nb = W2 / CB, lw = cx.flogW;
+        const long long n = (long long)cx.C * H * (W2 + 1);
+        for (long long e = gstart(); e < n; e += gstride()) {
+            const int c = (int)(e / ((long long)H * (W2 + 1)));
+            const int rem = (int)(e - (long long)c * H * (W2 + 1)), mu = rem / (W2 + 1), nu = rem - mu * (W2 + 1);
+            const int nupos = (int)(__brev((unsigned)nu) >> (32 - lw)) & (W - 1);
+            const float2 f = __ldcg(cx.fs + ((long long)c * H + mu) * W + nupos);
+            const float m2 = fmaf(f.x, f.x, f.y * f.y);
+            if (nu < W2) {
+                const int blk = nu / CB, k = nu - blk * CB;
+                const long long o = (((long long)c * nb + blk) * H + mu) * CB + k;
+                cx.fsh[o] = m2;
+                cx.fkh[o] = f;
+            } else {
+                cx.fsn[(long long)c * H + mu] = m2;
+                cx.fkn[(long long)c * H + mu] = f;
+            }
+        }
+    }
+
+    // Staged half spectra: row r of a task at r * spitch() + sidx(nu) (float2;
+    // two padding slots after every 32, against the bank conflicts of the
+    // bit-reversed reads of the first inverse pass; pairs stay 16-byte aligned)
+    __device__ int spitch() const { const int W2 = cx.W / 2; return W2 + 2 * (W2 >> 5); }
+    __device__ static int sidx(int nu) { return nu + 2 * (nu >> 5); }
+    __device__ int brevw(int v) const { return (int)(__brev((unsigned)v) >> (32 - cx.flogW)) & (cx.W - 1); }
+
+    // copies of row task t (rows i0 .. i0+2frp-1 of channel c), whole 16-byte
+    // copies: its half spectra into stage st, and the image rows i0-1 ..
+    // i0+2frp of buffer b1 followed by those of b2 (RF_HESS: again with the
+    // halo rows; RF_FISTA: the task's rows only) into the row buffer
+    __device__ void rtask_spc(int t, float *st)
+    {
+        const int W2 = cx.W / 2, RP = cx.frp, tpc = cx.H / (2 * RP), bd = blockDim.x;
+        const int c = t / tpc, i0 = (t - c * tpc) * 2 * RP;
+        float2 *sp = reinterpret_cast<float2 *>(st);
+        const float2 *z = cx.fzh + ((long long)c * cx.H + i0) * W2;
+        const int hq = W2 >> 1, spp = spitch();
+        for (int e = tid(); e < 2 * RP * hq; e += bd) {
+            const int r = e / hq, k2 = 2 * (e - r * hq);
+            cp_async16(sp + r * spp + sidx(k2), z + (long long)r * W2 + k2);
+        }
+        cp_async_commit();
+    }
+    __device__ void rtask_rows(int t, int mode, int b1, int b2)
+    {
+        const int W = cx.W, RP = cx.frp, tpc = cx.H / (2 * RP), bd = blockDim.x, q = W >> 2;
+        const int c = t / tpc, i0 = (t - c * tpc) * 2 * RP;
+        auto rows = [&](float *dst, int b, int r0, int nr) {
+            const T *src = buf(b) + c * cx.HWp + (long long)(r0 + cx.Gy) * cx.Wp + cx.Gx;
+            for (int e = tid(); e < nr * q; e += bd) {
+                const int r = e / q, k = e - r * q;
+                cp_async16(dst + r * W + 4 * k, src + (long long)r * cx.Wp + 4 * k);
+            }
+        };
+        float *rw = rrows();
+        rows(rw, b1, i0 - 1, 2 * RP + 2);
+        if (mode == RF_HESS) rows(rw + (2 * RP + 2) * W, b2, i0 - 1, 2 * RP + 2);
+        else rows(rw + (2 * RP + 2) * W, b2, i0, 2 * RP);
+        cp_async_commit();
+    }
+
+    // The row phase over all row tasks.  The inverse row transform starts from
+    // the staged half spectra (packing rows 2s, 2s+1 as Z = Y_a + i Y_b with
+    // Y[-nu] = conj Y[nu]); its last pass hands each thread's values to the
+    // per-pixel step in registers, which hands the next image's values on to
+    // the first forward pass:
+    //   RF_FWD:   forward row DFTs of buffer b1 into fzh / fzn.
+    //   RF_FISTA: G = B^T B y_k - B^T y_delta + alpha grad J(y_k), y_k in b1,
+    //             x_k in b2; x_{k+1} = y_k - tau_c G into bo1, y_{k+1} =
+    //             x_{k+1} + sc (x_{k+1} - x_k) into bo2 (with its ghosts);
+    //             forward row DFTs of y_{k+1}; returns sum G^2.
+    //   RF_CGP:   p = r + sc p_prev (r in b1, p_prev in b2; p = r when b2 < 0)
+    //             into bo1 (with its ghosts); forward row DFTs of p.
+    //   RF_HESS:  Hp = B^T B p + alpha D^T(phi''(D x) . D p), p in b1 (with
+    //             ghosts), x in b2, into bo1 (with its ghosts); returns sum p Hp.
+    __device__ S rows_r2c(int mode, int b1, int b2, int bo1, int bo2, T sc)
+    {
+        S part = Sc::zero();
+        if constexpr (kFFT) {
+            const int H = cx.H, W = cx.W, W2 = W / 2, lw = cx.flogW, RP = cx.frp, ps = cx.fpsh;
+            const int lrp = __ffs(RP) - 1, np = fft_npass(lw), spp = spitch();
+            const int tpc = H / (2 * RP), ntask = cx.C * tpc, bd = blockDim.x;
+            const float scale = 1.f / ((float)H * (float)W);
+            const T al = cx.alphaT, g = cx.rpT, ig = cx.irpT;
+            const T *tauc = tau();
+            float2 *wa = rwork();
+            T *O1 = bo1 >= 0 ? buf(bo1) : nullptr, *O2 = bo2 >= 0 ? buf(bo2) : nullptr;
+            const T *B1 = buf(b1), *B2 = b2 >= 0 ? buf(b2) : nullptr;
+            const bool inv = mode == RF_FISTA || mode == RF_HESS;
+            gedge = true;                  // every row has pixels whose copies live in the ghosts
+            auto slot = [=](int sq, int e) { return fslotp(sq, e, RP, ps); };
+            auto ld_wa = [=](int sq, int e, int) { return wa[slot(sq, e)]; };
+            auto st_wa = [=](int sq, int e, int, float2 v) { wa[slot(sq, e)] = v; };
+            auto nomid = [](int, int, int, auto &) {};
+            T sum = T(0);
+            int u = 0;
+            // copies: the next task's half spectra run under this task; this
+            // task's image rows run under its first inverse passes
+            const bool dbl = cx.fnst > 1;
+            if (inv && dbl && bid < ntask) rtask_spc(bid, rstage(0));
+            for (int t = bid; t < ntask; t += nblk, ++u) {
+                const int c = t / tpc, i0 = (t - c * tpc) * 2 * RP;
+                float *st = rstage(dbl ? (u & 1) : 0);
+                // with one spectrum stage the task's own spectrum goes first
+                const bool nxt = dbl && t + nblk < ntask;
+                if (inv) {
+                    if (!dbl) rtask_spc(t, st);
+                    rtask_rows(t, mode, b1, b2);
+                    if (nxt) rtask_spc(t + nblk, rstage((u + 1) & 1));
+                    if (nxt) cp_async_wait<2>();
+                    else cp_async_wait<1>();
+                }
+                __syncthreads();
+                const float2 *sp = reinterpret_cast<const float2 *>(st);
+                const float *rw = rrows();                          // rows i0-1 .. i0+2RP of b1, then b2's
+                auto rows_landed = [&]() {
+                    if (nxt) cp_async_wait<1>();
+                    else cp_async_wait<0>();
+                    __syncthreads();
+                };
+                const float2 *zn = cx.fzn + (long long)c * H + i0;
+                // the packed spectrum at bit-reversed position e (first inverse pass)
+                auto ld_pack = [=](int sq, int e, int) {
+                    const int nu = brevw(e);
+                    const float2 *ra = sp + (2 * sq) * spp, *rb = ra + spp;
+                    float2 ya, yv;
+                    if (nu < W2) {
+                        ya = ra[sidx(nu)];
+                        yv = rb[sidx(nu)];
+                    } else if (nu == W2) {
+                        ya = __ldcg(zn + 2 * sq);
+                        yv = __ldcg(zn + 2 * sq + 1);
+                    } else {
+                        const int mq = W - nu;
+                        ya = ra[sidx(mq)];
+                        yv = rb[sidx(mq)];
+                        ya.y = -ya.y;
+                        yv.y = -yv.y;
+                    }
+                    return make_float2(ya.x - yv.y, ya.y + yv.x);
+                };
+                auto lpass = [&](int i) { return fft_pass_len(lw, i); };
+                auto spass = [&](int i) { return fft_pass_s0(lw, i); };
+                if (mode == RF_FISTA) {
+                    const T tc = tauc[c];
+                    const float *xk = rw + (2 * RP + 2) * W;          // x_k, the task's rows
+                    auto ld_top = [&](int sq, int e, int m) { return np == 1 ? ld_pack(sq, e, m) : wa[slot(sq, e)]; };
+                    auto mid = [&](int sq, int base, int h, auto &v) {
+                        constexpr int R = sizeof(v) / sizeof(v[0]);
+#pragma unroll
+                        for (int m = 0; m < R; ++m) {
+                            const int j = base + m * h, jl = (j - 1) & (W - 1), jr = (j + 1) & (W - 1);
+                            float yo[2];
+#pragma unroll
+                            for (int pp = 0; pp < 2; ++pp) {
+                                const int r = 2 * sq + pp;
+                                const float *ym = rw + (r + 1) * W;
+                                const T yc = ym[j];
+                                const T tv = dphi<T>(cx.reg, yc - ym[jl], g, ig) - dphi<T>(cx.reg, ym[jr] - yc, g, ig) +
+                                             dphi<T>(cx.reg, yc - ym[j - W], g, ig) -
+                                             dphi<T>(cx.reg, ym[j + W] - yc, g, ig);
+                                // (B^T B y_k - B^T y_delta) from the inverse, + alpha grad J(y_k)
+                                const T gr = (pp ? v[m].y : v[m].x) * scale + al * tv;
+                                const T xnv = yc - tc * gr;
+                                const T ynv = xnv + sc * (xnv - xk[r * W + j]);
+                                O1[pidx(c, i0 + r, j)] = xnv;
+                                put(O2, c, i0 + r, j, ynv);
+                                sum += gr * gr;
+                                yo[pp] = ynv;
+                            }
+                            v[m] = make_float2(yo[0], yo[1]);
+                        }
+                    };
+                    for (int i = 0; i < np - 1; ++i) {
+                        if (i == 0) fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_pack, nomid, st_wa);
+                        else fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_wa, nomid, st_wa);
+                        __syncthreads();
+                    }
+                    rows_landed();
+                    fft_pass_n<2>(lpass(np - 1), W, RP, lrp, cx.ftwW, spass(np - 1), ld_top, mid, st_wa);
+                    __syncthreads();
+                } else if (mode == RF_HESS) {
+                    auto st_top = [&](int sq, int e, int, float2 v) {
+                        const int j = e, jl = (j - 1) & (W - 1), jr = (j + 1) & (W - 1);
+#pragma unroll
+                        for (int pp = 0; pp < 2; ++pp) {
+                            const int r = 2 * sq + pp, i = i0 + r;
+                            const float *pm = rw + (r + 1) * W, *xm = pm + (2 * RP + 2) * W;
+                            const T xc = xm[j], pc = pm[j];
+                            const T wl = ddphi<T>(cx.reg, xc - xm[jl], g, ig);
+                            const T wr = ddphi<T>(cx.reg, xm[jr] - xc, g, ig);
+                            const T wu = ddphi<T>(cx.reg, xc - xm[j - W], g, ig);
+                            const T wd = ddphi<T>(cx.reg, xm[j + W] - xc, g, ig);
+                            const T th = wl * (pc - pm[jl]) - wr * (pm[jr] - pc) + wu * (pc - pm[j - W]) -
+                                         wd * (pm[j + W] - pc);
+                            const T hv = (pp ? v.y : v.x) * scale + al * th;
+                            put(O1, c, i, j, hv);
+                            sum += hv * pc;
+                        }
+                    };
+                    for (int i = 0; i < np; ++i) {
+                        const bool top = i == np - 1;
+                        if (top) rows_landed();
+                        if (i == 0 && top) fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_pack, nomid, st_top);
+                        else if (i == 0) fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_pack, nomid, st_wa);
+                        else if (top) fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_wa, nomid, st_top);
+                        else fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_wa, nomid, st_wa);
+                        __syncthreads();
+                    }
+                    continue;                  // no forward transform
+                } else {
+                    // RF_FWD / RF_CGP: the first forward pass loads the image rows
+                    auto ld_img = [&](int sq, int e, int) {
+                        float pv[2];
+#pragma unroll
+                        for (int pp = 0; pp < 2; ++pp) {
+                            const int i = i0 + 2 * sq + pp;
+                            const long long o = pidx(c, i, e);
+                            if (mode == RF_CGP) {
+                                pv[pp] = B2 ? __ldcg(B1 + o) + sc * __ldcg(B2 + o) : __ldcg(B1 + o);
+                                put(O1, c, i, e, pv[pp]);
+                            } else {
+                                pv[pp] = __ldcg(B1 + o);
+                            }
+                        }
+                        return make_float2(pv[0], pv[1]);
+                    };
+                    fft_pass_n<0>(lpass(np - 1), W, RP, lrp, cx.ftwW, spass(np - 1), ld_img, nomid, st_wa);
+                    __syncthreads();
+                }
+                // the remaining forward passes, then separate the two rows'
+                // spectra and store nu = 0 .. W/2
+                for (int i = np - 2; i >= 0; --i) {
+                    fft_pass_n<0>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_wa, nomid, st_wa);
+                    __syncthreads();
+                }
+                float2 *zh = cx.fzh + ((long long)c * H + i0) * W2;
+                float2 *znw = cx.fzn + (long long)c * H + i0;
+                for (int e = tid(); e < RP * (W2 + 1); e += bd) {
+                    const int sq = e / (W2 + 1), nu = e - sq * (W2 + 1);
+                    const float2 z1 = wa[slot(sq, brevw(nu))];
+                    const float2 z2 = wa[slot(sq, brevw((W - nu) & (W - 1)))];
+                    const float2 xa = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
+                    const float2 xv = make_float2(0.5f * (z1.y + z2.y), -0.5f * (z1.x - z2.x));
+                    if (nu < W2) {
+                        zh[(2 * sq) * W2 + nu] = xa;
+                        zh[(2 * sq + 1) * W2 + nu] = xv;
+                    } else {
+                        znw[2 * sq] = xa;
+                        znw[2 * sq + 1] = xv;
+                    }
+                }
+                __syncthreads();               // the work area is rewritten by the next task
+            }
+            part = Sc::addv(part, sum);
+            cp_async_wait<0>();
+            fence_proxy_async_smem();      // before later phases' TMA copies into the same shared memory
+        }
+        return part;
+    }
+
+    // stage column task t (block blk of channel c, or the column W/2 of
+    // channel t - C*nb) into column stage buffer a: element (i, k) at
+    // fslot(k, i, cnt), 8-byte copies
+    __device__ void ctask_issue(int t, float2 *a)
+    {
+        const int H = cx.H, W2 = cx.W / 2, CB = cx.fcb2, nb = W2 / CB, lcb = __ffs(CB) - 1, bd = blockDim.x;
+        if (t < cx.C * nb) {
+            const int c = t / nb, blk = t - c * nb;
+            const float2 *z = cx.fzh + (long long)c * H * W2 + blk * CB;
+            for (int e = tid(); e < H * CB; e += bd) {
+                const int i = e >> lcb, k = e & (CB - 1);
+                cp_async8(a + fslot(k, i, CB), z + (long long)i * W2 + k);
+            }
+        } else {
+            const float2 *z = cx.fzn + (long long)(t - cx.C * nb) * H;
+            for (int i = tid(); i < H; i += bd) cp_async8(a + i, z + i);
+        }
+        cp_async_commit();
+    }
+
+    // The column phase over the half spectra in fzh / fzn:
+    //   CF_GRAM:  times |F(k)|^2 (B^T B);
+    //   CF_FISTA: times |F(k)|^2, minus F(B^T y_delta) from fch / fcn
+    //             (B^T B y - B^T y_delta, the smooth part of grad_x h);
+    //   CF_CY:    forward column transforms only, conj(F(k)) times them into
+    //             fch / fcn (F(B^T y) for an image y; fzh is left as it was).
+    // The last forward pass multiplies in registers and runs the first
+    // inverse stages; the last inverse pass stores to global memory.
+    enum { CF_GRAM = 0, CF_FISTA = 1, CF_CY = 2 };
+    __device__ void cols_r2c(int cmode = CF_GRAM)
+    {
+        if constexpr (kFFT) {
+            const int H = cx.H, lh = cx.flogH, W2 = cx.W / 2, CB = cx.fcb2, nb = W2 / CB;
+            const int ntask = cx.C * nb + cx.C, np = fft_npass(lh);
+            auto nomid = [](int, int, int, auto &) {};
+            int u = 0;
+            if (bid < ntask) ctask_issue(bid, cstage(0));
+            for (int t = bid; t < ntask; t += nblk, ++u) {
+                float2 *a = cstage(cx.fncs > 1 ? (u & 1) : 0);
+                const int tn = t + nblk;
+                if (cx.fncs == 1) {
+                    if (u > 0) ctask_issue(t, a);
+                    cp_async_wait<0>();
+                } else if (tn < ntask) {
+                    ctask_issue(tn, cstage((u + 1) & 1));
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                __syncthreads();
+                const bool nyq = t >= cx.C * nb;
+                const int cnt = nyq ? 1 : CB, lc = __ffs(cnt) - 1;
+                const int c = nyq ? t - cx.C * nb : t / nb, blk = nyq ? 0 : t - c * nb;
+                const long long tofs = nyq ? (long long)c * H : ((long long)c * nb + blk) * H * CB;
+                const float *sy = (nyq ? cx.fsn : cx.fsh) + tofs;
+                const float2 *ky = (nyq ? cx.fkn : cx.fkh) + tofs;
+                float2 *cy = (nyq ? cx.fcn : cx.fch) + tofs;
+                float2 *zg = nyq ? cx.fzn + (long long)c * H : cx.fzh + (long long)c * H * W2 + blk * CB;
+                const long long gst = nyq ? 1 : W2;
+                auto ld_a = [=](int sq, int e, int) { return a[fslot(sq, e, cnt)]; };
+                auto st_a = [=](int sq, int e, int, float2 v) { a[fslot(sq, e, cnt)] = v; };
+                auto st_g = [=](int sq, int e, int, float2 v) { zg[(long long)e * gst + sq] = v; };
+                auto st_cy = [=](int sq, int e, int, float2 v) {
+                    const long long o = (long long)e * cnt + sq;
+                    const float2 kv = __ldcg(ky + o);
+                    cy[o] = cmul(v, make_float2(kv.x, -kv.y));
+                };
+                auto sym = [=](int sq, int base, int h, auto &v) {
+                    constexpr int R = sizeof(v) / sizeof(v[0]);
+#pragma unroll
+                    for (int m = 0; m < R; ++m) {
+                        const long long o = (long long)(base + m * h) * cnt + sq;
+                        const float m2 = __ldcg(sy + o);
+                        if (cmode == CF_FISTA) {
+                            const float2 cv = __ldcg(cy + o);
+                            v[m] = make_float2(fmaf(v[m].x, m2, -cv.x), fmaf(v[m].y, m2, -cv.y));
+                        } else {
+                            v[m] = make_float2(v[m].x * m2, v[m].y * m2);
+                        }
+                    }
+                };
+                auto lpass = [&](int i) { return fft_pass_len(lh, i); };
+                auto spass = [&](int i) { return fft_pass_s0(lh, i); };
+                for (int i = np - 1; i >= 1; --i) {    // forward passes but the last
+                    fft_pass_n<0>(lpass(i), H, cnt, lc, cx.ftwH, spass(i), ld_a, nomid, st_a);
+                    __syncthreads();
+                }
+                if (cmode == CF_CY) {
+                    fft_pass_n<0>(lpass(0), H, cnt, lc, cx.ftwH, spass(0), ld_a, nomid, st_cy);
+                } else if (np == 1) {
+                    fft_pass_n<3>(lpass(0), H, cnt, lc, cx.ftwH, spass(0), ld_a, sym, st_g);
+                } else {
+                    fft_pass_n<3>(lpass(0), H, cnt, lc, cx.ftwH, spass(0), ld_a, sym, st_a);
+                    __syncthreads();
+                    for (int i = 1; i < np; ++i) {
+                        if (i == np - 1) fft_pass_n<1>(lpass(i), H, cnt, lc, cx.ftwH, spass(i), ld_a, nomid, st_g);
+                        else fft_pass_n<1>(lpass(i), H, cnt, lc, cx.ftwH, spass(i), ld_a, nomid, st_a);
+                        __syncthreads();
+                    }
+                }
+                __syncthreads();           // the buffer is refilled two tasks later
+            }
+            cp_async_wait<0>();
+            fence_proxy_async_smem();
+        }
+    }
+
+    // FISTA of lower_solve on the real-to-complex pipeline: the same
+    // iterates, stopping test and cap as the direct path (the test on
+    // ||grad_x h(y_k)|| is read during the column phase of iteration k)
+    __device__ int lower_solve_r2c(const T *b, int bin, int bout, double eps, int max_iters, double &gn,
+                                   long long &passes)
+    {
+        load_weights(b);               // spectrum and Gram symbol of b
+        compute_tau(b);
+        copy_buf(B_X0, B_Y0, bin);
+        if (!sync()) return 0;
+        // F(B^T y_delta) = conj(F(k)) F(y_delta), once per solve
+        rows_r2c(RF_FWD, B_Y, -1, -1, -1, T(0));
+        if (!sync()) return 0;
+        cols_r2c(CF_CY);
+        if (!sync()) return 0;
+        rows_r2c(RF_FWD, B_Y0, -1, -1, -1, T(0));
+        if (!sync()) return 0;
+        cols_r2c(CF_FISTA);
+        if (!sync()) return 0;
+        int xp = B_X0, xn = B_X1, yc = B_Y0, yn = B_Y1;
+        const S eps2 = Sc::from_double(eps * eps);
+        S t = Sc::of(1);
+        S tn = next_t(t);
+        T th = (T)Sc::to_elem(Sc::div(Sc::addv(t, -1), tn));
+        int result = yc, k = 0;
+        for (;; ++k) {
+            const S part = rows_r2c(RF_FISTA, yc, xp, xn, yn, th);
+            const S cta = block_sum<T>(part, red());
+            if (tid() == 0) partS(k & 1)[bid] = cta;
+            const S t_next = tn;
+            const S tn_next = next_t(t_next);
+            const T th_next = (T)Sc::to_elem(Sc::div(Sc::addv(t_next, -1), tn_next));
+            if (!sync()) return k;
+            passes += 1;
+            if (k >= max_iters) {
+                const S ss = grid_total<T>(partS(k & 1), nblk, gbuf(), bcast());
+                if (!Sc::finite(ss)) {
+                    if (tid() == 0) raise(ST_NONFINITE);
+                    alive = false;
+                    return k;
+                }
+                gn = sqrt(Sc::to_double(ss));
+                result = yc;
+                break;
+            }
+            if (warp == 0) grid_issue<T>(partS(k & 1), nblk, gbuf());
+            cols_r2c(CF_FISTA);
+            if (warp == 0) {
+                const S s = grid_finish<T>(nblk, gbuf());
+                if (lane == 0) *bcast() = s;
+            }
+            __syncthreads();
+            const S ss = *bcast();
+            __syncthreads();
+            if (!Sc::finite(ss)) {
+                if (tid() == 0) raise(ST_NONFINITE);
+                alive = false;
+                return k;
+            }
+            if (Sc::le(ss, eps2)) {        // y_k passes: x_{k+1}, y_{k+1} are dropped
+                gn = sqrt(Sc::to_double(ss));
+                result = yc;
+                break;
+            }
+            if (!sync()) return k;
+            t = t_next;
+            tn = tn_next;
+            th = th_next;
+            int tmp = xp; xp = xn; xn = tmp;
+            tmp = yc; yc = yn; yn = tmp;
+        }
+        if (result != bout) copy_buf(bout, -1, result);
+        return k;
     }
 
     // pass() on the FFT path: the correlation comes from fft_conv, then the
@@ -590,7 +1124,7 @@ struct Eng {
     __device__ S pass(bool flip, int img0, int img1, int t1b, int t2b, int fb, Prep prep, Epi epi)
     {
         if constexpr (kFFT) {
-            if (cx.fft) return pass_fft(flip ? FM_B : FM_BT, img0, t1b, t2b, fb, epi);   // img1 is never set here
+            return pass_fft(flip ? FM_B : FM_BT, img0, t1b, t2b, fb, epi);   // img1 is never set here
         }
         S part = Sc::zero();
         if (!alive || tmafail) return part;
@@ -794,7 +1328,7 @@ struct Eng {
     // (the FISTA gradient and the Hessian products)
     __device__ bool gram() const
     {
-        if constexpr (kFFT) return cx.fft != 0;
+        if constexpr (kFFT) return true;
         else return false;
     }
 
@@ -831,6 +1365,9 @@ struct Eng {
     __device__ int lower_solve(const T *b, int bin, int bout, double eps, int max_iters, double &gn,
                                long long &passes)
     {
+        if constexpr (kFFT) {
+            if (cx.fr2c) return lower_solve_r2c(b, bin, bout, eps, max_iters, gn, passes);
+        }
         load_weights(b);
         compute_tau(b);
         copy_buf(B_X0, B_Y0, bin);
@@ -997,6 +1534,9 @@ struct Eng {
     __device__ int cg(const T *b, int bx, int brhs, double delta, int max_iters, bool zero_start, double &res,
                       int &capped, long long &passes)
     {
+        if constexpr (kFFT) {
+            if (cx.fr2c) return cg_r2c(b, bx, brhs, delta, max_iters, zero_start, res, capped, passes);
+        }
         load_weights(b);
         T *R = buf(B_R), *HP = buf(B_HP), *Q = buf(B_Q);
         const T *RHS = buf(brhs);
@@ -1139,6 +1679,135 @@ struct Eng {
         return it;
     }
 
+    // CG of Algorithm 1 (step 2) on the real-to-complex pipeline: per
+    // iteration the direction update with its forward row transforms, the
+    // column phase, the inverse row transforms with the TV Hessian term and
+    // <p, H p>, then the same element-wise update of q and r as cg()
+    __device__ int cg_r2c(const T *b, int bx, int brhs, double delta, int max_iters, bool zero_start, double &res,
+                      int &capped, long long &passes)
+    {
+        load_weights(b);
+        T *R = buf(B_R), *HP = buf(B_HP), *Q = buf(B_Q);
+        const T *RHS = buf(brhs);
+        int pc = B_P0, po = B_P1;
+        if (!zero_start) {             // HP = H q for the initial residual
+            rows_r2c(RF_FWD, B_Q, -1, -1, -1, T(0));
+            if (!sync()) return 0;
+            cols_r2c();
+            if (!sync()) return 0;
+            rows_r2c(RF_HESS, B_Q, bx, B_HP, -1, T(0));
+            if (!sync()) return 0;
+            passes += 1;
+        }
+        auto interior = [&](int row, int j) {
+            const int pi = row % cx.Hp;
+            return pi >= cx.Gy && pi < cx.Gy + cx.H && j >= cx.Gx && j < cx.Gx + cx.W;
+        };
+        S rrp = Sc::zero();
+        {
+            T *PCb = buf(pc);
+            for (int row = gw(); row < cx.C * cx.Hp; row += TW()) {
+                const long long rb = (long long)row * cx.Wp;
+                T s = T(0);
+                for (int j0 = 0; j0 < cx.Wp; j0 += 32 * EWB) {
+                    T v[EWB];
+#pragma unroll
+                    for (int u = 0; u < EWB; ++u) {
+                        const int j = j0 + u * 32 + lane;
+                        v[u] = j < cx.Wp ? (zero_start ? __ldcg(RHS + rb + j) : __ldcg(RHS + rb + j) - __ldcg(HP + rb + j))
+                                         : T(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < EWB; ++u) {
+                        const int j = j0 + u * 32 + lane;
+                        if (j < cx.Wp) {
+                            if (zero_start) Q[rb + j] = T(0);
+                            R[rb + j] = v[u];
+                            PCb[rb + j] = v[u];
+                            if (interior(row, j)) s += v[u] * v[u];
+                        }
+                    }
+                }
+                rrp = Sc::addv(rrp, s);
+            }
+        }
+        S rr = reduce(rrp, 4);
+        if (!alive) return 0;
+        const S delta2 = Sc::from_double(delta * delta);
+        int it = 0;
+        capped = 0;
+        bool first = true;
+        T beta = T(0);
+        while (!Sc::le(rr, delta2) && it < max_iters) {
+            // p = r + beta p (p = r, already in place, at the first iteration)
+            // with its forward row transforms; the column phase; H p and <p, H p>
+            if (first) rows_r2c(RF_FWD, pc, -1, -1, -1, T(0));
+            else rows_r2c(RF_CGP, B_R, po, pc, -1, beta);
+            if (!sync()) return it;
+            cols_r2c();
+            if (!sync()) return it;
+            const S php = reduce(rows_r2c(RF_HESS, pc, bx, B_HP, -1, T(0)), 5);
+            if (!alive) return it;
+            passes += 1;
+            if (!Sc::finite(php)) {
+                if (tid() == 0) raise(ST_NONFINITE);
+                alive = false;
+                return it;
+            }
+            if (!Sc::positive(php)) { capped = 1; break; }
+            const T a = (T)Sc::to_elem(Sc::div(rr, php));
+            S rn = Sc::zero();
+            {
+                const T *PCr = buf(pc);
+                for (int row = gw(); row < cx.C * cx.Hp; row += TW()) {
+                    const long long rb = (long long)row * cx.Wp;
+                    T s = T(0);
+                    for (int j0 = 0; j0 < cx.Wp; j0 += 32 * EWB) {
+                        T pv[EWB], qv[EWB], rv[EWB], hv[EWB];
+#pragma unroll
+                        for (int u = 0; u < EWB; ++u) {
+                            const int j = j0 + u * 32 + lane;
+                            if (j < cx.Wp) {
+                                pv[u] = __ldcg(PCr + rb + j);
+                                qv[u] = __ldcg(Q + rb + j);
+                                rv[u] = __ldcg(R + rb + j);
+                                hv[u] = __ldcg(HP + rb + j);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < EWB; ++u) {
+                            const int j = j0 + u * 32 + lane;
+                            if (j < cx.Wp) {
+                                Q[rb + j] = qv[u] + a * pv[u];
+                                const T r2 = rv[u] - a * hv[u];
+                                R[rb + j] = r2;
+                                if (interior(row, j)) s += r2 * r2;
+                            }
+                        }
+                    }
+                    rn = Sc::addv(rn, s);
+                }
+            }
+            const S rr_new = reduce(rn, 6);
+            if (!alive) return it;
+            ++it;
+            if (!Sc::finite(rr_new)) {
+                if (tid() == 0) raise(ST_NONFINITE);
+                alive = false;
+                return it;
+            }
+            if (Sc::le(rr_new, delta2)) { rr = rr_new; break; }
+            beta = (T)Sc::to_elem(Sc::div(rr_new, rr));
+            rr = rr_new;
+            po = pc;
+            pc = (pc == B_P0) ? B_P1 : B_P0;
+            first = false;
+        }
+        res = sqrt(Sc::to_double(rr));
+        if (!Sc::le(rr, delta2)) capped = 1;
+        return it;
+    }
+
     // out[c,p,q] = sum_ij x[c,i-p+r,j-q+r] (B v)[c,i,j] + v[c,i-p+r,j-q+r] (B x - y)[c,i,j]
     // (Algorithm 1, step 3, with the sign of Eq. 3.2: z = -out (+ grad r(b)));
     // x, v in buffers bx, bv; written to zout; returns ||zout||^2
@@ -1150,11 +1819,13 @@ struct Eng {
         const int CKK = cx.C * KK;
         S *zall = reinterpret_cast<S *>(cx.zpart);
         S *zp = zall + (long long)gw() * CKK;
-        for (int e = lane; e < CKK; e += 32) zp[e] = Sc::zero();
+        if constexpr (!kFFT) {         // per-warp lag-sum rows (the direct path's phase K2)
+            for (int e = lane; e < CKK; e += 32) zp[e] = Sc::zero();
+        }
         // phase K1: U = B v, V = B x - y (image pixels only: phase K2 reads
         // interiors).  The stages of v and then of x run through the same
         // double buffer.  On the FFT path: two passes.
-        if (kFFT && cx.fft) {
+        if (kFFT) {
             pass(true, bv, -1, -1, -1, -1, noprep, [=](int c, int gi, int gj, long long, int, T v, T) {
                 U[pidx(c, gi, gj)] = v;
                 return T(0);
@@ -1206,7 +1877,7 @@ struct Eng {
             for (long long e = gstart(); e < CKK; e += gstride()) {
                 const int c = (int)(e / KK), pq = (int)(e - (long long)c * KK), p = pq / K, q = pq - p * K;
                 const int i = ((p - r) % H + H) % H, j = ((q - r) % W + W) % W;
-                double zz = (double)__ldcg(cx.fout + (long long)c * cx.HW + (long long)i * W + j);
+                double zz = (double)__ldcg(cx.fout + (long long)c * cx.HW + (long long)i * W + j) + cross_off()[c];
                 if (negate) zz = -zz;
                 if (add_r) zz += grad_sobolev_elem(b, (int)e);
                 zout[e] = (T)zz;
@@ -1563,7 +2234,8 @@ __device__ __forceinline__ void run_program(Eng<T, FFTP> &e, const Ctx<T> &cx, c
 
 // One problem per launch: the launch record lives in parameter space.
 template <typename T, bool FFTP = false>
-__global__ void __launch_bounds__(MAXNW * 32, 1) adp_kernel(const __grid_constant__ Ctx<T> cx,
+__global__ void __launch_bounds__((FFTP ? FFT_WARPS : MAXNW) * 32, FFTP ? FFT_CTAS_PER_SM : 1)
+    adp_kernel(const __grid_constant__ Ctx<T> cx,
                                                             const __grid_constant__ Job<T> jb)
 {
     ADP_KERNEL_SMEM;

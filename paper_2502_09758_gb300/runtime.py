@@ -1,7 +1,8 @@
 """Host-side runtime around the library's calls: checkpoint/resume of the
-MAID state, a per-iteration log, and the operator-path autotuner.  Every step
-of the method runs in the library (adp.py binds it); this module only stores,
-records and times those calls."""
+MAID state, a per-iteration log, and the autotuners of the operator path and
+of the direct path's launch shape.  Every step of the method runs in the
+library (adp.py binds it); this module only stores, records and times those
+calls."""
 from __future__ import annotations
 
 import numpy as np
@@ -25,18 +26,65 @@ def choose_operator_path(prob, b, x, iters=8, reps=2):
             if e.status != ADP_EINVAL:
                 raise
             continue
-        best = float("inf")
-        for _ in range(reps):
-            t = []
-            for n in (iters, 2 * iters):
-                xs = x.clone()
-                prob.lower_solve(b, xs, 0.0, n)
-                t.append(prob.last_kernel_ms())
-            best = min(best, (t[1] - t[0]) / iters)
-        per[path] = best
+        per[path] = _fista_ms(prob, b, x, iters, reps)
     choice = min(per, key=per.get)
     prob.set_fft(choice == "fft")
     return {"path": choice, **{f"{k}_ms": v for k, v in per.items()}}
+
+
+def _fista_ms(prob, b, x, iters, reps):
+    """Per-update device time of FISTA (launches of iters and 2 iters updates
+    with eps = 0, so that the per-solve set-up cancels), best of reps."""
+    best = float("inf")
+    for _ in range(reps):
+        t = []
+        for n in (iters, 2 * iters):
+            xs = x.clone()
+            prob.lower_solve(b, xs, 0.0, n)
+            t.append(prob.last_kernel_ms())
+        best = min(best, (t[1] - t[0]) / iters)
+    return best
+
+
+def launch_candidates(nstrips, nsm=152, max_ctas=512):
+    """(grid, warps per CTA) shapes for the direct path's launch-shape
+    autotuner: for 8, 6, 4 and 2 warps, the grid that gives every warp one
+    strip (when it fits), one CTA per SM and the multiples of the SM count up
+    to the strips' need.  Strips are 32 x MR pixels, dealt to warps in order,
+    so a shape whose warp count divides the strips evenly leaves no warp idle
+    in the last round."""
+    out = []
+    for nw in (8, 6, 4, 2):
+        need = -(-nstrips // nw)
+        grids = {min(nsm, need), min(need, max_ctas)}
+        grids |= {k * nsm for k in (2, 3) if k * nsm <= min(need, max_ctas)}
+        for g in sorted(grids):
+            if g >= 1 and (g, nw) not in out:
+                out.append((g, nw))
+    return out
+
+
+def choose_launch(prob, b, x, iters=8, reps=2, nsm=152):
+    """Autotune the direct path's launch shape (adp_set_launch): time FISTA
+    updates at the problem's own shape and at every candidate shape the device
+    accepts, and keep the fastest.  Returns {"grid": ..., "nw": ...,
+    "ms": {(grid, nw): per-update ms}}."""
+    pr = prob.params
+    mr = 8 if pr.prec == 1 else 4                    # strip rows: FP32 8, FP64 4
+    nstrips = pr.C * (-(-pr.H // mr)) * (-(-pr.W // 32))
+    start = (prob.grid_size(), prob.warps_per_cta())
+    per = {}
+    for g, nw in [start] + [c for c in launch_candidates(nstrips, nsm) if c != start]:
+        try:
+            prob.set_launch(g, nw)
+        except AdpError as e:
+            if e.status != ADP_EINVAL:
+                raise
+            continue
+        per[(g, nw)] = _fista_ms(prob, b, x, iters, reps)
+    choice = min(per, key=per.get) if per else start
+    prob.set_launch(*choice)
+    return {"grid": choice[0], "nw": choice[1], "ms": per}
 
 
 def save_maid_checkpoint(path, state: adp_maid_state, b, x, q, **meta):
