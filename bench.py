@@ -671,7 +671,12 @@ def run_ours(args):
         peak_tf = 1.25
     flops = passes * 2.0 * K * K * N
     achieved = flops / (kern_ms / 1e3) / 1e12
-    traffic = committed_traffic("maid_run_rgb256_k15_traffic.json", MAID_SOURCES) if not fft else None
+    if fft:
+        traffic = (committed_traffic("maid_run_rgb2048_k63_traffic.json", FFT_SOURCES)
+                   if spec["name"] == WORKLOAD else None)
+    else:
+        traffic = (committed_traffic("maid_run_rgb256_k15_traffic.json", MAID_SOURCES)
+                   if spec["name"] == "rgb256_k15_motion" else None)
     if fft:   # FFT path: bound by memory traffic
         hbm = float(pk.get("hbm_gbs", 6787.2))
         r2c = prob.fft_pipeline() == 2
@@ -756,6 +761,7 @@ def run_ours(args):
 
 
 MAID_SOURCES = ("adp.cu", "adp_device.cuh", "adp_engine.cuh", "adp_f32.cu", "adp_f32b.cu")
+FFT_SOURCES = ("adp.cu", "adp_device.cuh", "adp_engine.cuh", "adp_fft.cuh", "adp_f32fft.cu")
 TC_SOURCES = ("adp_tc.cu", "adp_tc.cuh", "adp_device.cuh")
 
 

@@ -721,7 +721,6 @@ struct Eng {
             auto ld_wa = [=](int sq, int e, int) { return wa[slot(sq, e)]; };
             auto st_wa = [=](int sq, int e, int, float2 v) { wa[slot(sq, e)] = v; };
             auto nomid = [](int, int, int, auto &) {};
-            T sum = T(0);
             int u = 0;
             // copies: the next task's half spectra run under this task; this
             // task's image rows run under its first inverse passes
@@ -776,6 +775,7 @@ struct Eng {
                     auto ld_top = [&](int sq, int e, int m) { return np == 1 ? ld_pack(sq, e, m) : wa[slot(sq, e)]; };
                     auto mid = [&](int sq, int base, int h, auto &v) {
                         constexpr int R = sizeof(v) / sizeof(v[0]);
+                        T gs = T(0);           // this group's share of ||G||^2 (FP32, then float-float)
 #pragma unroll
                         for (int m = 0; m < R; ++m) {
                             const int j = base + m * h, jl = (j - 1) & (W - 1), jr = (j + 1) & (W - 1);
@@ -794,11 +794,12 @@ struct Eng {
                                 const T ynv = xnv + sc * (xnv - xk[r * W + j]);
                                 O1[pidx(c, i0 + r, j)] = xnv;
                                 put(O2, c, i0 + r, j, ynv);
-                                sum += gr * gr;
+                                gs += gr * gr;
                                 yo[pp] = ynv;
                             }
                             v[m] = make_float2(yo[0], yo[1]);
                         }
+                        part = Sc::addv(part, gs);
                     };
                     for (int i = 0; i < np - 1; ++i) {
                         if (i == 0) fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_pack, nomid, st_wa);
@@ -811,6 +812,7 @@ struct Eng {
                 } else if (mode == RF_HESS) {
                     auto st_top = [&](int sq, int e, int, float2 v) {
                         const int j = e, jl = (j - 1) & (W - 1), jr = (j + 1) & (W - 1);
+                        T ps2[2];
 #pragma unroll
                         for (int pp = 0; pp < 2; ++pp) {
                             const int r = 2 * sq + pp, i = i0 + r;
@@ -824,8 +826,9 @@ struct Eng {
                                          wd * (pm[j + W] - pc);
                             const T hv = (pp ? v.y : v.x) * scale + al * th;
                             put(O1, c, i, j, hv);
-                            sum += hv * pc;
+                            ps2[pp] = hv * pc;
                         }
+                        part = Sc::addv(part, ps2[0] + ps2[1]);
                     };
                     for (int i = 0; i < np; ++i) {
                         const bool top = i == np - 1;
@@ -881,7 +884,6 @@ struct Eng {
                 }
                 __syncthreads();               // the work area is rewritten by the next task
             }
-            part = Sc::addv(part, sum);
             cp_async_wait<0>();
             fence_proxy_async_smem();      // before later phases' TMA copies into the same shared memory
         }
