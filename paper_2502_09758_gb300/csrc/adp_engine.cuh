@@ -180,6 +180,34 @@ struct Eng {
         if (ox && oy) B[o + ox + oy] = v;
     }
 
+    // Every ghost copy of rows i0 .. i0+nr-1 of channel c of B: each padded
+    // position (ii, jj) with ii = i (mod H) and jj = j (mod W), other than
+    // the pixel (i, j) itself, gets val(i - i0, j).  The same positions as
+    // put() writes for every pixel of those rows (all threads take part).
+    template <typename V>
+    __device__ void ghost_rows(T *B, int c, int i0, int nr, V val) const
+    {
+        const int H = cx.H, W = cx.W, Gx = cx.Gx, Gy = cx.Gy, Wg = W + 2 * Gx;
+        T *base = B + c * cx.HWp;
+        auto col = [=](int jj) { const int js = jj % W; return js < 0 ? js + W : js; };
+        // the ghost columns of the rows themselves
+        for (int q = threadIdx.x; q < nr * 2 * Gx; q += blockDim.x) {
+            const int r = q / (2 * Gx), k = q - r * 2 * Gx, jj = k < Gx ? k - Gx : W + k - Gx;
+            base[(long long)(i0 + r + Gy) * cx.Wp + jj + Gx] = val(r, col(jj));
+        }
+        // whole ghost rows: row i has copies at i + m H (m != 0) only when
+        // i < Gy or i >= H - Gy
+        for (int r = 0; r < nr; ++r) {
+            const int i = i0 + r;
+            if (i >= Gy && i < H - Gy) continue;
+            for (int ii = i - ((i + Gy) / H) * H; ii < H + Gy; ii += H) {
+                if (ii == i) continue;
+                T *row = base + (long long)(ii + Gy) * cx.Wp;   // image column -Gx at row[0]
+                for (int q = threadIdx.x; q < Wg; q += blockDim.x) row[q] = val(r, col(q - Gx));
+            }
+        }
+    }
+
     __device__ void strip_of(int s, int &c, int &row0, int &col0)
     {
         const int per = cx.nx * cx.ny;
@@ -604,7 +632,7 @@ struct Eng {
     //                 transform of (B^T B y_k)'s half spectra, the gradient
     //                 G = B^T B y_k - B^T y_delta + alpha grad J(y_k), the
     //                 updates x_{k+1}, y_{k+1} and the forward row transform of
-    //                 y_{k+1} happen in one pass over the rows.
+    //                 y_{k+1} happen in one visit of the rows.
     //   column phase: per block of fcb2 half-spectrum columns, the forward
     //                 column transform, the product with |F(k)|^2 (the symbol
     //                 of B^T B, real), the inverse column transform.
@@ -690,9 +718,10 @@ struct Eng {
 
     // The row phase over all row tasks.  The inverse row transform starts from
     // the staged half spectra (packing rows 2s, 2s+1 as Z = Y_a + i Y_b with
-    // Y[-nu] = conj Y[nu]); its last pass hands each thread's values to the
-    // per-pixel step in registers, which hands the next image's values on to
-    // the first forward pass:
+    // Y[-nu] = conj Y[nu]) and leaves the rows in the work area in natural
+    // order; the per-pixel step reads them there (RF_HESS: in the last
+    // inverse pass's stores), and the forward transform starts from the
+    // values it writes back:
     //   RF_FWD:   forward row DFTs of buffer b1 into fzh / fzn.
     //   RF_FISTA: G = B^T B y_k - B^T y_delta + alpha grad J(y_k), y_k in b1,
     //             x_k in b2; x_{k+1} = y_k - tau_c G into bo1, y_{k+1} =
@@ -722,18 +751,25 @@ struct Eng {
             auto st_wa = [=](int sq, int e, int, float2 v) { wa[slot(sq, e)] = v; };
             auto nomid = [](int, int, int, auto &) {};
             int u = 0;
-            // copies: the next task's half spectra run under this task; this
-            // task's image rows run under its first inverse passes
+            // copies, double buffered: the next task's half spectra run under
+            // this whole task, its image rows under this task's forward passes
+            // (issued once the row buffer is free).  Single buffered: the
+            // task's own spectrum, then its rows, at the task's start.  Either
+            // way the groups complete in the order spectrum(t), rows(t), ...
             const bool dbl = cx.fnst > 1;
-            if (inv && dbl && bid < ntask) rtask_spc(bid, rstage(0));
+            if (inv && dbl && bid < ntask) {
+                rtask_spc(bid, rstage(0));
+                rtask_rows(bid, mode, b1, b2);
+            }
             for (int t = bid; t < ntask; t += nblk, ++u) {
                 const int c = t / tpc, i0 = (t - c * tpc) * 2 * RP;
                 float *st = rstage(dbl ? (u & 1) : 0);
-                // with one spectrum stage the task's own spectrum goes first
                 const bool nxt = dbl && t + nblk < ntask;
                 if (inv) {
-                    if (!dbl) rtask_spc(t, st);
-                    rtask_rows(t, mode, b1, b2);
+                    if (!dbl) {
+                        rtask_spc(t, st);
+                        rtask_rows(t, mode, b1, b2);
+                    }
                     if (nxt) rtask_spc(t + nblk, rstage((u + 1) & 1));
                     if (nxt) cp_async_wait<2>();
                     else cp_async_wait<1>();
@@ -772,42 +808,76 @@ struct Eng {
                 if (mode == RF_FISTA) {
                     const T tc = tauc[c];
                     const float *xk = rw + (2 * RP + 2) * W;          // x_k, the task's rows
-                    auto ld_top = [&](int sq, int e, int m) { return np == 1 ? ld_pack(sq, e, m) : wa[slot(sq, e)]; };
-                    auto mid = [&](int sq, int base, int h, auto &v) {
-                        constexpr int R = sizeof(v) / sizeof(v[0]);
-                        T gs = T(0);           // this group's share of ||G||^2 (FP32, then float-float)
-#pragma unroll
-                        for (int m = 0; m < R; ++m) {
-                            const int j = base + m * h, jl = (j - 1) & (W - 1), jr = (j + 1) & (W - 1);
-                            float yo[2];
-#pragma unroll
-                            for (int pp = 0; pp < 2; ++pp) {
-                                const int r = 2 * sq + pp;
-                                const float *ym = rw + (r + 1) * W;
-                                const T yc = ym[j];
-                                const T tv = dphi<T>(cx.reg, yc - ym[jl], g, ig) - dphi<T>(cx.reg, ym[jr] - yc, g, ig) +
-                                             dphi<T>(cx.reg, yc - ym[j - W], g, ig) -
-                                             dphi<T>(cx.reg, ym[j + W] - yc, g, ig);
-                                // (B^T B y_k - B^T y_delta) from the inverse, + alpha grad J(y_k)
-                                const T gr = (pp ? v[m].y : v[m].x) * scale + al * tv;
-                                const T xnv = yc - tc * gr;
-                                const T ynv = xnv + sc * (xnv - xk[r * W + j]);
-                                O1[pidx(c, i0 + r, j)] = xnv;
-                                put(O2, c, i0 + r, j, ynv);
-                                gs += gr * gr;
-                                yo[pp] = ynv;
-                            }
-                            v[m] = make_float2(yo[0], yo[1]);
-                        }
-                        part = Sc::addv(part, gs);
-                    };
-                    for (int i = 0; i < np - 1; ++i) {
+                    for (int i = 0; i < np; ++i) {
                         if (i == 0) fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_pack, nomid, st_wa);
                         else fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_wa, nomid, st_wa);
                         __syncthreads();
                     }
                     rows_landed();
-                    fft_pass_n<2>(lpass(np - 1), W, RP, lrp, cx.ftwW, spass(np - 1), ld_top, mid, st_wa);
+                    // the per-pixel step in natural order, four consecutive
+                    // pixels of both rows of a pair per thread: B^T B y_k -
+                    // B^T y_delta from the inverse, + alpha grad J(y_k);
+                    // x_{k+1}, y_{k+1} to global memory (interior, 16-byte
+                    // stores); y_{k+1} back into the work area for the forward
+                    // transform
+                    auto pixels = [&](auto regc) {
+                        constexpr int REG = decltype(regc)::value;
+                        const int lq = lw - 2, q4 = W >> 2;
+                        for (int e = tid(); e < RP * q4; e += bd) {
+                            const int sq = e >> lq, j0 = (e & (q4 - 1)) << 2;
+                            float2 z[4];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) z[q] = wa[slot(sq, j0 + q)];
+                            float yo[2][4];
+                            T gs = T(0);       // this thread's share of ||G||^2 (FP32, then float-float)
+#pragma unroll
+                            for (int pp = 0; pp < 2; ++pp) {
+                                const int r = 2 * sq + pp;
+                                const float *ym = rw + (r + 1) * W;
+                                const float4 yc4 = *reinterpret_cast<const float4 *>(ym + j0);
+                                const float4 yu4 = *reinterpret_cast<const float4 *>(ym - W + j0);
+                                const float4 yd4 = *reinterpret_cast<const float4 *>(ym + W + j0);
+                                const float4 xk4 = *reinterpret_cast<const float4 *>(xk + r * W + j0);
+                                const float ys[6] = {ym[(j0 - 1) & (W - 1)], yc4.x, yc4.y, yc4.z, yc4.w,
+                                                     ym[(j0 + 4) & (W - 1)]};
+                                const float yu[4] = {yu4.x, yu4.y, yu4.z, yu4.w};
+                                const float yd[4] = {yd4.x, yd4.y, yd4.z, yd4.w};
+                                const float xq[4] = {xk4.x, xk4.y, xk4.z, xk4.w};
+                                float xo[4];
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) {
+                                    const T yc = ys[q + 1];
+                                    const T tv = dphi<T>(REG, yc - ys[q], g, ig) - dphi<T>(REG, ys[q + 2] - yc, g, ig) +
+                                                 dphi<T>(REG, yc - yu[q], g, ig) - dphi<T>(REG, yd[q] - yc, g, ig);
+                                    const T gr = (pp ? z[q].y : z[q].x) * scale + al * tv;
+                                    const T xnv = yc - tc * gr;
+                                    xo[q] = xnv;
+                                    yo[pp][q] = xnv + sc * (xnv - xq[q]);
+                                    gs += gr * gr;
+                                }
+                                const int o = pidx(c, i0 + r, j0);
+                                *reinterpret_cast<float4 *>(O1 + o) = make_float4(xo[0], xo[1], xo[2], xo[3]);
+                                *reinterpret_cast<float4 *>(O2 + o) =
+                                    make_float4(yo[pp][0], yo[pp][1], yo[pp][2], yo[pp][3]);
+                            }
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) wa[slot(sq, j0 + q)] = make_float2(yo[0][q], yo[1][q]);
+                            part = Sc::addv(part, gs);
+                        }
+                    };
+                    if (cx.reg == 0) pixels(std::integral_constant<int, 0>());
+                    else if (cx.reg == 1) pixels(std::integral_constant<int, 1>());
+                    else pixels(std::integral_constant<int, 2>());
+                    __syncthreads();
+                    ghost_rows(O2, c, i0, 2 * RP, [&](int r, int j) {
+                        const float2 z = wa[slot(r >> 1, j)];
+                        return (r & 1) ? z.y : z.x;
+                    });
+                    // the row buffer is free: the next task's rows load under
+                    // the forward passes
+                    if (nxt) rtask_rows(t + nblk, mode, b1, b2);
+                    __syncthreads();               // the ghost copies have read the work area
+                    fft_pass_n<0>(lpass(np - 1), W, RP, lrp, cx.ftwW, spass(np - 1), ld_wa, nomid, st_wa);
                     __syncthreads();
                 } else if (mode == RF_HESS) {
                     auto st_top = [&](int sq, int e, int, float2 v) {
@@ -839,6 +909,7 @@ struct Eng {
                         else fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_wa, nomid, st_wa);
                         __syncthreads();
                     }
+                    if (nxt) rtask_rows(t + nblk, mode, b1, b2);
                     continue;                  // no forward transform
                 } else {
                     // RF_FWD / RF_CGP: the first forward pass loads the image rows
@@ -916,14 +987,14 @@ struct Eng {
     //             (B^T B y - B^T y_delta, the smooth part of grad_x h);
     //   CF_CY:    forward column transforms only, conj(F(k)) times them into
     //             fch / fcn (F(B^T y) for an image y; fzh is left as it was).
-    // The last forward pass multiplies in registers and runs the first
-    // inverse stages; the last inverse pass stores to global memory.
+    // The product runs between the forward and the inverse passes, over the
+    // staged spectrum; the last inverse pass stores to global memory.
     enum { CF_GRAM = 0, CF_FISTA = 1, CF_CY = 2 };
     __device__ void cols_r2c(int cmode = CF_GRAM)
     {
         if constexpr (kFFT) {
             const int H = cx.H, lh = cx.flogH, W2 = cx.W / 2, CB = cx.fcb2, nb = W2 / CB;
-            const int ntask = cx.C * nb + cx.C, np = fft_npass(lh);
+            const int ntask = cx.C * nb + cx.C, np = fft_npass(lh), bd = blockDim.x;
             auto nomid = [](int, int, int, auto &) {};
             int u = 0;
             if (bid < ntask) ctask_issue(bid, cstage(0));
@@ -957,20 +1028,6 @@ struct Eng {
                     const float2 kv = __ldcg(ky + o);
                     cy[o] = cmul(v, make_float2(kv.x, -kv.y));
                 };
-                auto sym = [=](int sq, int base, int h, auto &v) {
-                    constexpr int R = sizeof(v) / sizeof(v[0]);
-#pragma unroll
-                    for (int m = 0; m < R; ++m) {
-                        const long long o = (long long)(base + m * h) * cnt + sq;
-                        const float m2 = __ldcg(sy + o);
-                        if (cmode == CF_FISTA) {
-                            const float2 cv = __ldcg(cy + o);
-                            v[m] = make_float2(fmaf(v[m].x, m2, -cv.x), fmaf(v[m].y, m2, -cv.y));
-                        } else {
-                            v[m] = make_float2(v[m].x * m2, v[m].y * m2);
-                        }
-                    }
-                };
                 auto lpass = [&](int i) { return fft_pass_len(lh, i); };
                 auto spass = [&](int i) { return fft_pass_s0(lh, i); };
                 for (int i = np - 1; i >= 1; --i) {    // forward passes but the last
@@ -979,12 +1036,39 @@ struct Eng {
                 }
                 if (cmode == CF_CY) {
                     fft_pass_n<0>(lpass(0), H, cnt, lc, cx.ftwH, spass(0), ld_a, nomid, st_cy);
-                } else if (np == 1) {
-                    fft_pass_n<3>(lpass(0), H, cnt, lc, cx.ftwH, spass(0), ld_a, sym, st_g);
                 } else {
-                    fft_pass_n<3>(lpass(0), H, cnt, lc, cx.ftwH, spass(0), ld_a, sym, st_a);
+                    fft_pass_n<0>(lpass(0), H, cnt, lc, cx.ftwH, spass(0), ld_a, nomid, st_a);
                     __syncthreads();
-                    for (int i = 1; i < np; ++i) {
+                    // the symbol product in the order of the global arrays:
+                    // element (mu, k) of the task at mu * cnt + k, so that
+                    // consecutive threads read consecutive words; the loads of
+                    // four elements go out before their products
+                    const int n = H * cnt;
+                    for (int e0 = tid(); e0 < n; e0 += 4 * bd) {
+                        float m2[4];
+                        float2 cv[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int e = e0 + q * bd;
+                            if (e < n) {
+                                m2[q] = __ldcg(sy + e);
+                                if (cmode == CF_FISTA) cv[q] = __ldcg(cy + e);
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int e = e0 + q * bd;
+                            if (e < n) {
+                                float2 &v = a[fslot(e & (cnt - 1), e >> lc, cnt)];
+                                if (cmode == CF_FISTA)
+                                    v = make_float2(fmaf(v.x, m2[q], -cv[q].x), fmaf(v.y, m2[q], -cv[q].y));
+                                else
+                                    v = make_float2(v.x * m2[q], v.y * m2[q]);
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    for (int i = 0; i < np; ++i) {
                         if (i == np - 1) fft_pass_n<1>(lpass(i), H, cnt, lc, cx.ftwH, spass(i), ld_a, nomid, st_g);
                         else fft_pass_n<1>(lpass(i), H, cnt, lc, cx.ftwH, spass(i), ld_a, nomid, st_a);
                         __syncthreads();
