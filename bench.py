@@ -84,8 +84,8 @@ WORKLOAD_SPECS = {
 }
 # algorithmic bytes per value of the FFT path's phases (FP32): a FISTA
 # iteration on the real-to-complex pipeline (row phase: half spectrum 4, y_k 4,
-# x_k 4 in, x_{k+1} 4, y_{k+1} 4, half spectrum 4 out; column phase: half
-# spectrum 4 + 4, |F(k)|^2 2, F(B^T y) 4: 38 in all), a CG iteration (direction update and
+# x_k 4, B^T y 4 in, x_{k+1} 4, y_{k+1} 4, half spectrum 4 out; column phase:
+# half spectrum 4 + 4, |F(k)|^2 2: 38 in all), a CG iteration (direction update and
 # its forward rows 16, column phase 10, inverse rows with the Hessian 16, the
 # element-wise update of q and r 24), and any other convolution pass on the
 # complex pipeline (FFT_BYTES_PER_VALUE)

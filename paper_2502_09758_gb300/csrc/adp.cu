@@ -99,8 +99,6 @@ struct adp_problem {
     int fr2c, frp, fcb2, fpsh, fnst, fncs, fstage, fcstage, frows;
     float2 *fzh, *fzn;      // half spectra (C x H x W/2) and the column W/2 (C x H)
     float *fsh, *fsn;       // |F(k)|^2 at those columns
-    float2 *fkh, *fkn;      // F(k) at those columns
-    float2 *fch, *fcn;      // F(B^T y_delta) of the current lower solve
 };
 
 // ------------------------------------------------------------ tensor maps
@@ -203,7 +201,6 @@ static Ctx<T> make_ctx(const adp_problem *p)
         c.fr2c = p->fr2c; c.frp = p->frp; c.fcb2 = p->fcb2; c.fpsh = p->fpsh; c.fnst = p->fnst;
         c.fstage = p->fstage; c.fcstage = p->fcstage; c.frows = p->frows; c.fncs = p->fncs;
         c.fzh = p->fzh; c.fzn = p->fzn; c.fsh = p->fsh; c.fsn = p->fsn;
-        c.fkh = p->fkh; c.fkn = p->fkn; c.fch = p->fch; c.fcn = p->fcn;
     }
     return c;
 }
@@ -283,8 +280,7 @@ void adp_problem_destroy(adp_problem *p)
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
     tc_plan_destroy(p->tc);
-    void *fptrs[] = {p->fz, p->fs, p->fy, p->ftw, p->fout, p->fc, p->fzh, p->fzn, p->fsh, p->fsn,
-                     p->fkh, p->fkn, p->fch, p->fcn};
+    void *fptrs[] = {p->fz, p->fs, p->fy, p->ftw, p->fout, p->fc, p->fzh, p->fzn, p->fsh, p->fsn};
     for (void *q : fptrs) if (q) cudaFree(q);
     free(p->a_host);
     free(p);
@@ -581,7 +577,9 @@ adp_status adp_set_fft(adp_problem *p, int enable)
     if (q.W >= 4 && enable != 2) {
         // shared memory of a row task with rp row pairs: its half spectra
         // double buffered (2 rp rows of W/2 + 2 (W/64) float2 each), one buffer
-        // of 4 rp + 4 image rows, the work area; of a column task: two stages
+        // of 6 rp + 2 image rows (FISTA: y with its halo, x, B^T y; the
+        // Hessian product: p and x with their halos), the work area; of a
+        // column task: two stages of its spectrum and of its symbol
         const size_t spp = (size_t)(q.W / 2) + 2 * (size_t)(q.W / 64);
         const int W2 = q.W / 2;
         int best_rp = 0, cb2 = 0, nst = 0, ncs = 0;
@@ -594,7 +592,7 @@ adp_status adp_set_fft(adp_problem *p, int enable)
                 int lrp = 0;
                 while ((1 << lrp) < rp) ++lrp;
                 const int psr = lw + lrp >= 9 ? lw + lrp - 5 : 31;
-                const size_t spc = 4 * (size_t)rp * spp, rows = (size_t)(4 * rp + 4) * q.W;     // floats
+                const size_t spc = 4 * (size_t)rp * spp, rows = (size_t)(6 * rp + 2) * q.W;     // floats
                 const size_t work = ((size_t)rp * q.W + (((size_t)rp * q.W) >> psr) + 1) * 8;  // bytes
                 if ((ns * spc + rows) * 4 + work > scratch) break;
                 best_rp = rp;
@@ -605,7 +603,7 @@ adp_status adp_set_fft(adp_problem *p, int enable)
             }
         for (int ns = 2; ns >= 1 && best_rp && !cb2; --ns)
             for (int c2 = W2 < 16 ? W2 : 16; c2 >= 2; c2 >>= 1) {
-                if ((size_t)ns * q.H * c2 * 8 > scratch) continue;
+                if ((size_t)ns * q.H * c2 * 12 > scratch) continue;   // float2 spectrum + float symbol
                 if (c2 > 2 && (long long)q.C * (W2 / c2) < grid_fft) continue;
                 cb2 = c2;
                 ncs = ns;
@@ -626,10 +624,6 @@ adp_status adp_set_fft(adp_problem *p, int enable)
                 CK(cudaMalloc((void **)&p->fzn, nn * sizeof(float2)));
                 CK(cudaMalloc((void **)&p->fsh, nh * sizeof(float)));
                 CK(cudaMalloc((void **)&p->fsn, nn * sizeof(float)));
-                CK(cudaMalloc((void **)&p->fkh, nh * sizeof(float2)));
-                CK(cudaMalloc((void **)&p->fkn, nn * sizeof(float2)));
-                CK(cudaMalloc((void **)&p->fch, nh * sizeof(float2)));
-                CK(cudaMalloc((void **)&p->fcn, nn * sizeof(float2)));
             }
             p->fr2c = 1;
         }

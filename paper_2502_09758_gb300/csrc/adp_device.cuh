@@ -289,6 +289,12 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
 }
 
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
@@ -572,8 +578,6 @@ struct Ctx {
     int frows;                         // floats of the row tasks' image-row buffer
     float2 *fzh, *fzn;                 // half spectra C x H x W/2 (columns 0 .. W/2-1) and the column W/2, C x H
     float *fsh, *fsn;                  // |F(k)|^2 at those columns: tiled per column task, and at W/2
-    float2 *fkh, *fkn;                 // F(k) itself, same layout
-    float2 *fch, *fcn;                 // F(B^T y_delta) of the current lower solve, same layout
 };
 
 template <typename T>

@@ -632,12 +632,13 @@ struct Eng {
     //                 transform of (B^T B y_k)'s half spectra, the gradient
     //                 G = B^T B y_k - B^T y_delta + alpha grad J(y_k), the
     //                 updates x_{k+1}, y_{k+1} and the forward row transform of
-    //                 y_{k+1} happen in one visit of the rows.
+    //                 y_{k+1} happen in one visit of the rows (B^T y_delta is
+    //                 an image, computed once per solve).
     //   column phase: per block of fcb2 half-spectrum columns, the forward
     //                 column transform, the product with |F(k)|^2 (the symbol
     //                 of B^T B, real), the inverse column transform.
-    // Operands are staged into shared memory with cp.async (16-byte copies)
-    // in fnst buffers, so that the next task's loads run under the current
+    // Operands are staged into shared memory with cp.async, double buffered
+    // where they fit, so that the next task's loads run under the current
     // task's transforms.
     enum { RF_FWD = 0, RF_FISTA = 1, RF_CGP = 2, RF_HESS = 3 };
 
@@ -645,13 +646,13 @@ struct Eng {
     __device__ float *rstage(int k) const { return reinterpret_cast<float *>(fft_scratch()) + k * cx.fstage; }
     __device__ float *rrows() const { return rstage(cx.fnst); }
     __device__ float2 *rwork() const { return reinterpret_cast<float2 *>(rrows() + cx.frows); }
-    // column phase: two stages
+    // column phase: fncs stages of the half spectra
     __device__ float2 *cstage(int k) const { return fft_scratch() + k * cx.fcstage; }
 
-    // |F(k)|^2 and F(k) at the half-spectrum columns from the complex spectrum
-    // cx.fs (bit-reversed along both axes): fsh / fkh[((c*nb + blk)*H + mu)*fcb2 + k]
-    // at column nu = blk*fcb2 + k, fsn / fkn[c*H + mu] at nu = W/2 (bit-reversed
-    // row position mu, the order of the column phase's forward transform)
+    // |F(k)|^2 at the half-spectrum columns from the complex spectrum cx.fs
+    // (bit-reversed along both axes): fsh[((c*nb + blk)*H + mu)*fcb2 + k] at
+    // column nu = blk*fcb2 + k, fsn[c*H + mu] at nu = W/2 (bit-reversed row
+    // position mu, the order of the column phase's forward transform)
     __device__ void gram_symbol()
     {
         const int H = cx.H, W = cx.W, W2 = W / 2, CB = cx.fcb2, nb = W2 / CB, lw = cx.flogW;
@@ -666,10 +667,8 @@ struct Eng {
                 const int blk = nu / CB, k = nu - blk * CB;
                 const long long o = (((long long)c * nb + blk) * H + mu) * CB + k;
                 cx.fsh[o] = m2;
-                cx.fkh[o] = f;
             } else {
                 cx.fsn[(long long)c * H + mu] = m2;
-                cx.fkn[(long long)c * H + mu] = f;
             }
         }
     }
@@ -684,7 +683,8 @@ struct Eng {
     // copies of row task t (rows i0 .. i0+2frp-1 of channel c), whole 16-byte
     // copies: its half spectra into stage st, and the image rows i0-1 ..
     // i0+2frp of buffer b1 followed by those of b2 (RF_HESS: again with the
-    // halo rows; RF_FISTA: the task's rows only) into the row buffer
+    // halo rows; RF_FISTA: the task's rows only, then those of c = B^T y_delta)
+    // into the row buffer
     __device__ void rtask_spc(int t, float *st)
     {
         const int W2 = cx.W / 2, RP = cx.frp, tpc = cx.H / (2 * RP), bd = blockDim.x;
@@ -711,8 +711,15 @@ struct Eng {
         };
         float *rw = rrows();
         rows(rw, b1, i0 - 1, 2 * RP + 2);
-        if (mode == RF_HESS) rows(rw + (2 * RP + 2) * W, b2, i0 - 1, 2 * RP + 2);
-        else rows(rw + (2 * RP + 2) * W, b2, i0, 2 * RP);
+        if (mode == RF_HESS) {
+            rows(rw + (2 * RP + 2) * W, b2, i0 - 1, 2 * RP + 2);
+        } else {
+            rows(rw + (2 * RP + 2) * W, b2, i0, 2 * RP);
+            // RF_FISTA: rows i0 .. i0+2frp-1 of c = B^T y_delta (dense, contiguous)
+            const float *cs = cx.fc + ((long long)c * cx.H + i0) * W;
+            float *cd = rw + (4 * RP + 2) * W;
+            for (int e = tid(); e < 2 * RP * q; e += bd) cp_async16(cd + 4 * e, cs + 4 * e);
+        }
         cp_async_commit();
     }
 
@@ -724,7 +731,7 @@ struct Eng {
     // values it writes back:
     //   RF_FWD:   forward row DFTs of buffer b1 into fzh / fzn.
     //   RF_FISTA: G = B^T B y_k - B^T y_delta + alpha grad J(y_k), y_k in b1,
-    //             x_k in b2; x_{k+1} = y_k - tau_c G into bo1, y_{k+1} =
+    //             x_k in b2, B^T y_delta in cx.fc; x_{k+1} = y_k - tau_c G into bo1, y_{k+1} =
     //             x_{k+1} + sc (x_{k+1} - x_k) into bo2 (with its ghosts);
     //             forward row DFTs of y_{k+1}; returns sum G^2.
     //   RF_CGP:   p = r + sc p_prev (r in b1, p_prev in b2; p = r when b2 < 0)
@@ -808,6 +815,7 @@ struct Eng {
                 if (mode == RF_FISTA) {
                     const T tc = tauc[c];
                     const float *xk = rw + (2 * RP + 2) * W;          // x_k, the task's rows
+                    const float *cr = rw + (4 * RP + 2) * W;          // c = B^T y_delta, the task's rows
                     for (int i = 0; i < np; ++i) {
                         if (i == 0) fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_pack, nomid, st_wa);
                         else fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_wa, nomid, st_wa);
@@ -815,8 +823,8 @@ struct Eng {
                     }
                     rows_landed();
                     // the per-pixel step in natural order, four consecutive
-                    // pixels of both rows of a pair per thread: B^T B y_k -
-                    // B^T y_delta from the inverse, + alpha grad J(y_k);
+                    // pixels of both rows of a pair per thread: B^T B y_k from
+                    // the inverse, - B^T y_delta, + alpha grad J(y_k);
                     // x_{k+1}, y_{k+1} to global memory (interior, 16-byte
                     // stores); y_{k+1} back into the work area for the forward
                     // transform
@@ -838,18 +846,20 @@ struct Eng {
                                 const float4 yu4 = *reinterpret_cast<const float4 *>(ym - W + j0);
                                 const float4 yd4 = *reinterpret_cast<const float4 *>(ym + W + j0);
                                 const float4 xk4 = *reinterpret_cast<const float4 *>(xk + r * W + j0);
+                                const float4 c4 = *reinterpret_cast<const float4 *>(cr + r * W + j0);
                                 const float ys[6] = {ym[(j0 - 1) & (W - 1)], yc4.x, yc4.y, yc4.z, yc4.w,
                                                      ym[(j0 + 4) & (W - 1)]};
                                 const float yu[4] = {yu4.x, yu4.y, yu4.z, yu4.w};
                                 const float yd[4] = {yd4.x, yd4.y, yd4.z, yd4.w};
                                 const float xq[4] = {xk4.x, xk4.y, xk4.z, xk4.w};
+                                const float cq[4] = {c4.x, c4.y, c4.z, c4.w};
                                 float xo[4];
 #pragma unroll
                                 for (int q = 0; q < 4; ++q) {
                                     const T yc = ys[q + 1];
                                     const T tv = dphi<T>(REG, yc - ys[q], g, ig) - dphi<T>(REG, ys[q + 2] - yc, g, ig) +
                                                  dphi<T>(REG, yc - yu[q], g, ig) - dphi<T>(REG, yd[q] - yc, g, ig);
-                                    const T gr = (pp ? z[q].y : z[q].x) * scale + al * tv;
+                                    const T gr = (pp ? z[q].y : z[q].x) * scale - cq[q] + al * tv;
                                     const T xnv = yc - tc * gr;
                                     xo[q] = xnv;
                                     yo[pp][q] = xnv + sc * (xnv - xq[q]);
@@ -961,51 +971,64 @@ struct Eng {
         return part;
     }
 
+    // column phase: fncs stages of the half spectra, then as many of the symbol
+    __device__ float *csym(int k) const { return reinterpret_cast<float *>(cstage(cx.fncs)) + (long long)k * cx.fcstage; }
+
     // stage column task t (block blk of channel c, or the column W/2 of
-    // channel t - C*nb) into column stage buffer a: element (i, k) at
-    // fslot(k, i, cnt), 8-byte copies
-    __device__ void ctask_issue(int t, float2 *a)
+    // channel t - C*nb) into column stage k: element (i, k) of the spectrum at
+    // fslot(k, i, cnt) (8-byte copies), the symbol |F(k)|^2 of its columns in
+    // the order of fsh / fsn (16-byte copies where whole)
+    __device__ void ctask_issue(int t, int k)
     {
         const int H = cx.H, W2 = cx.W / 2, CB = cx.fcb2, nb = W2 / CB, lcb = __ffs(CB) - 1, bd = blockDim.x;
+        float2 *a = cstage(k);
+        float *sm = csym(k);
+        const float *sy;
+        int n;
         if (t < cx.C * nb) {
             const int c = t / nb, blk = t - c * nb;
             const float2 *z = cx.fzh + (long long)c * H * W2 + blk * CB;
             for (int e = tid(); e < H * CB; e += bd) {
-                const int i = e >> lcb, k = e & (CB - 1);
-                cp_async8(a + fslot(k, i, CB), z + (long long)i * W2 + k);
+                const int i = e >> lcb, kk = e & (CB - 1);
+                cp_async8(a + fslot(kk, i, CB), z + (long long)i * W2 + kk);
             }
+            sy = cx.fsh + ((long long)c * nb + blk) * H * CB;
+            n = H * CB;
         } else {
             const float2 *z = cx.fzn + (long long)(t - cx.C * nb) * H;
             for (int i = tid(); i < H; i += bd) cp_async8(a + i, z + i);
+            sy = cx.fsn + (long long)(t - cx.C * nb) * H;
+            n = H;
         }
+        if ((n & 3) == 0)
+            for (int e = 4 * tid(); e < n; e += 4 * bd) cp_async16(sm + e, sy + e);
+        else
+            for (int e = tid(); e < n; e += bd) cp_async4(sm + e, sy + e);
         cp_async_commit();
     }
 
-    // The column phase over the half spectra in fzh / fzn:
-    //   CF_GRAM:  times |F(k)|^2 (B^T B);
-    //   CF_FISTA: times |F(k)|^2, minus F(B^T y_delta) from fch / fcn
-    //             (B^T B y - B^T y_delta, the smooth part of grad_x h);
-    //   CF_CY:    forward column transforms only, conj(F(k)) times them into
-    //             fch / fcn (F(B^T y) for an image y; fzh is left as it was).
-    // The product runs between the forward and the inverse passes, over the
-    // staged spectrum; the last inverse pass stores to global memory.
-    enum { CF_GRAM = 0, CF_FISTA = 1, CF_CY = 2 };
-    __device__ void cols_r2c(int cmode = CF_GRAM)
+    // The column phase over the half spectra in fzh / fzn: forward column
+    // transforms, the product with |F(k)|^2 (the symbol of B^T B, staged with
+    // the task's spectrum) over the staged spectrum, inverse column
+    // transforms; the last inverse pass stores to global memory.
+    __device__ void cols_r2c()
     {
         if constexpr (kFFT) {
             const int H = cx.H, lh = cx.flogH, W2 = cx.W / 2, CB = cx.fcb2, nb = W2 / CB;
             const int ntask = cx.C * nb + cx.C, np = fft_npass(lh), bd = blockDim.x;
             auto nomid = [](int, int, int, auto &) {};
             int u = 0;
-            if (bid < ntask) ctask_issue(bid, cstage(0));
+            if (bid < ntask) ctask_issue(bid, 0);
             for (int t = bid; t < ntask; t += nblk, ++u) {
-                float2 *a = cstage(cx.fncs > 1 ? (u & 1) : 0);
+                const int sk = cx.fncs > 1 ? (u & 1) : 0;
+                float2 *a = cstage(sk);
+                const float *sm = csym(sk);
                 const int tn = t + nblk;
                 if (cx.fncs == 1) {
-                    if (u > 0) ctask_issue(t, a);
+                    if (u > 0) ctask_issue(t, 0);
                     cp_async_wait<0>();
                 } else if (tn < ntask) {
-                    ctask_issue(tn, cstage((u + 1) & 1));
+                    ctask_issue(tn, (u + 1) & 1);
                     cp_async_wait<1>();
                 } else {
                     cp_async_wait<0>();
@@ -1014,67 +1037,30 @@ struct Eng {
                 const bool nyq = t >= cx.C * nb;
                 const int cnt = nyq ? 1 : CB, lc = __ffs(cnt) - 1;
                 const int c = nyq ? t - cx.C * nb : t / nb, blk = nyq ? 0 : t - c * nb;
-                const long long tofs = nyq ? (long long)c * H : ((long long)c * nb + blk) * H * CB;
-                const float *sy = (nyq ? cx.fsn : cx.fsh) + tofs;
-                const float2 *ky = (nyq ? cx.fkn : cx.fkh) + tofs;
-                float2 *cy = (nyq ? cx.fcn : cx.fch) + tofs;
                 float2 *zg = nyq ? cx.fzn + (long long)c * H : cx.fzh + (long long)c * H * W2 + blk * CB;
                 const long long gst = nyq ? 1 : W2;
                 auto ld_a = [=](int sq, int e, int) { return a[fslot(sq, e, cnt)]; };
                 auto st_a = [=](int sq, int e, int, float2 v) { a[fslot(sq, e, cnt)] = v; };
                 auto st_g = [=](int sq, int e, int, float2 v) { zg[(long long)e * gst + sq] = v; };
-                auto st_cy = [=](int sq, int e, int, float2 v) {
-                    const long long o = (long long)e * cnt + sq;
-                    const float2 kv = __ldcg(ky + o);
-                    cy[o] = cmul(v, make_float2(kv.x, -kv.y));
-                };
                 auto lpass = [&](int i) { return fft_pass_len(lh, i); };
                 auto spass = [&](int i) { return fft_pass_s0(lh, i); };
-                for (int i = np - 1; i >= 1; --i) {    // forward passes but the last
+                for (int i = np - 1; i >= 0; --i) {
                     fft_pass_n<0>(lpass(i), H, cnt, lc, cx.ftwH, spass(i), ld_a, nomid, st_a);
                     __syncthreads();
                 }
-                if (cmode == CF_CY) {
-                    fft_pass_n<0>(lpass(0), H, cnt, lc, cx.ftwH, spass(0), ld_a, nomid, st_cy);
-                } else {
-                    fft_pass_n<0>(lpass(0), H, cnt, lc, cx.ftwH, spass(0), ld_a, nomid, st_a);
-                    __syncthreads();
-                    // the symbol product in the order of the global arrays:
-                    // element (mu, k) of the task at mu * cnt + k, so that
-                    // consecutive threads read consecutive words; the loads of
-                    // four elements go out before their products
-                    const int n = H * cnt;
-                    for (int e0 = tid(); e0 < n; e0 += 4 * bd) {
-                        float m2[4];
-                        float2 cv[4];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int e = e0 + q * bd;
-                            if (e < n) {
-                                m2[q] = __ldcg(sy + e);
-                                if (cmode == CF_FISTA) cv[q] = __ldcg(cy + e);
-                            }
-                        }
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int e = e0 + q * bd;
-                            if (e < n) {
-                                float2 &v = a[fslot(e & (cnt - 1), e >> lc, cnt)];
-                                if (cmode == CF_FISTA)
-                                    v = make_float2(fmaf(v.x, m2[q], -cv[q].x), fmaf(v.y, m2[q], -cv[q].y));
-                                else
-                                    v = make_float2(v.x * m2[q], v.y * m2[q]);
-                            }
-                        }
-                    }
-                    __syncthreads();
-                    for (int i = 0; i < np; ++i) {
-                        if (i == np - 1) fft_pass_n<1>(lpass(i), H, cnt, lc, cx.ftwH, spass(i), ld_a, nomid, st_g);
-                        else fft_pass_n<1>(lpass(i), H, cnt, lc, cx.ftwH, spass(i), ld_a, nomid, st_a);
-                        __syncthreads();
-                    }
+                // element (mu, k) of the task: symbol at mu * cnt + k
+                for (int e = tid(); e < H * cnt; e += bd) {
+                    float2 &v = a[fslot(e & (cnt - 1), e >> lc, cnt)];
+                    const float m2 = sm[e];
+                    v = make_float2(v.x * m2, v.y * m2);
                 }
-                __syncthreads();           // the buffer is refilled two tasks later
+                __syncthreads();
+                for (int i = 0; i < np; ++i) {
+                    if (i == np - 1) fft_pass_n<1>(lpass(i), H, cnt, lc, cx.ftwH, spass(i), ld_a, nomid, st_g);
+                    else fft_pass_n<1>(lpass(i), H, cnt, lc, cx.ftwH, spass(i), ld_a, nomid, st_a);
+                    __syncthreads();
+                }
+                __syncthreads();           // the buffers are refilled two tasks later
             }
             cp_async_wait<0>();
             fence_proxy_async_smem();
@@ -1091,14 +1077,11 @@ struct Eng {
         compute_tau(b);
         copy_buf(B_X0, B_Y0, bin);
         if (!sync()) return 0;
-        // F(B^T y_delta) = conj(F(k)) F(y_delta), once per solve
-        rows_r2c(RF_FWD, B_Y, -1, -1, -1, T(0));
-        if (!sync()) return 0;
-        cols_r2c(CF_CY);
-        if (!sync()) return 0;
+        // c = B^T y_delta (dense, in cx.fc), once per solve, on the complex pipeline
+        if (!fft_conv(FM_BT, B_Y, cx.fc)) return 0;
         rows_r2c(RF_FWD, B_Y0, -1, -1, -1, T(0));
         if (!sync()) return 0;
-        cols_r2c(CF_FISTA);
+        cols_r2c();
         if (!sync()) return 0;
         int xp = B_X0, xn = B_X1, yc = B_Y0, yn = B_Y1;
         const S eps2 = Sc::from_double(eps * eps);
@@ -1127,7 +1110,7 @@ struct Eng {
                 break;
             }
             if (warp == 0) grid_issue<T>(partS(k & 1), nblk, gbuf());
-            cols_r2c(CF_FISTA);
+            cols_r2c();
             if (warp == 0) {
                 const S s = grid_finish<T>(nblk, gbuf());
                 if (lane == 0) *bcast() = s;
