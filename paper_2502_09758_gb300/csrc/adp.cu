@@ -87,6 +87,7 @@ struct adp_problem {
     long long *trace;      // optional barrier trace (2 * trace_cap values)
     int trace_cap;
     CUtensorMap map_s, map_1, map_i;
+    CUtensorMap map_fz;     // FFT path: the half spectra fzh as a 2-D FP32 tensor
     cudaEvent_t ev0, ev1;  // bracket the cooperative launch on the problem's stream
     float last_ms;
     TcPlan *tc;            // BF16 tensor-core operator workspace (made on first use)
@@ -180,7 +181,7 @@ static Ctx<T> make_ctx(const adp_problem *p)
     memset(&c, 0, sizeof c);
     const adp_params &q = p->prm;
     const Geom &g = p->g;
-    c.map_s = p->map_s; c.map_1 = p->map_1; c.map_i = p->map_i;
+    c.map_s = p->map_s; c.map_1 = p->map_1; c.map_i = p->map_i; c.map_fz = p->map_fz;
     c.C = q.C; c.H = q.H; c.W = q.W; c.K = q.K; c.r = g.r; c.Kp = g.Kp;
     c.r4 = g.r4; c.Gx = g.Gx; c.Gy = g.Gy; c.Wp = g.Wp; c.Hp = g.Hp; c.BW = g.BW;
     c.nx = g.nx; c.ny = g.ny; c.nstrips = g.nstrips; c.wsm = g.wsm; c.multiwrap = g.multiwrap;
@@ -603,7 +604,8 @@ adp_status adp_set_fft(adp_problem *p, int enable)
             }
         for (int ns = 2; ns >= 1 && best_rp && !cb2; --ns)
             for (int c2 = W2 < 16 ? W2 : 16; c2 >= 2; c2 >>= 1) {
-                if ((size_t)ns * q.H * c2 * 12 > scratch) continue;   // float2 spectrum + float symbol
+                // float2 spectrum + float symbol, stages rounded to 128 bytes (TMA destinations)
+                if ((size_t)ns * (((size_t)q.H * c2 + 15) / 16 * 16) * 12 > scratch) continue;
                 if (c2 > 2 && (long long)q.C * (W2 / c2) < grid_fft) continue;
                 cb2 = c2;
                 ncs = ns;
@@ -616,7 +618,7 @@ adp_status adp_set_fft(adp_problem *p, int enable)
             p->fncs = ncs;
             p->fstage = (int)st_spc;
             p->frows = (int)st_rows;
-            p->fcstage = q.H * cb2;
+            p->fcstage = (q.H * cb2 + 15) / 16 * 16;
             p->fcb2 = cb2;
             if (!p->fzh) {
                 const size_t nh = (size_t)q.C * q.H * W2, nn = (size_t)q.C * q.H;
@@ -624,6 +626,23 @@ adp_status adp_set_fft(adp_problem *p, int enable)
                 CK(cudaMalloc((void **)&p->fzn, nn * sizeof(float2)));
                 CK(cudaMalloc((void **)&p->fsh, nh * sizeof(float)));
                 CK(cudaMalloc((void **)&p->fsn, nn * sizeof(float)));
+            }
+            // fzh as FP32 [C*H][W]: a column task's block is the box of
+            // 2 fcb2 floats x min(H, 256) rows, H / that many boxes per task
+            {
+                char emsg[160];
+                EncodeTiledFn fn = encode_fn(emsg, sizeof emsg);
+                if (!fn) return set_err(ADP_ECUDA, "%s", emsg);
+                const cuuint64_t dims[2] = {(cuuint64_t)q.W, (cuuint64_t)q.C * q.H};
+                const cuuint64_t strides[1] = {(cuuint64_t)W2 * sizeof(float2)};
+                const cuuint32_t box[2] = {(cuuint32_t)(2 * cb2), (cuuint32_t)(q.H < 256 ? q.H : 256)};
+                const cuuint32_t estr[2] = {1, 1};
+                const CUresult r = fn(&p->map_fz, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->fzh, dims, strides, box, estr,
+                                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS)
+                    return set_err(ADP_ECUDA, "tensor map encoding (half spectra) failed%s with CUresult %lld", "",
+                                   (long long)r);
             }
             p->fr2c = 1;
         }

@@ -391,6 +391,43 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *mbar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
 }
 
+// Untiled bulk copies (both addresses 16-byte aligned, bytes a multiple of
+// 16): global to this CTA's shared memory, completion counted on mbar; and
+// shared to global in a bulk group of the issuing thread.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+// tiled 2-D copies of a box of a 2-D tensor map (x innermost, 16-byte aligned)
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(mbar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, const void *src)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(x),
+                 "r"(y), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the issuing thread's bulk groups: all have finished reading their shared sources
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// ... and have completed their writes
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int w,
                                             uint64_t *mbar)
 {
@@ -539,6 +576,7 @@ enum Buf : int {
 template <typename T>
 struct Ctx {
     CUtensorMap map_s, map_1, map_i;   // boxes: stage (BW x NX), halo-1 tile (40 x MR+2), interior (32 x MR)
+    CUtensorMap map_fz;                // FFT path: fzh as FP32 [C*H][W] (box 2 fcb2 x min(H, 256))
     int C, H, W, K, r, Kp;             // Kp: kernel rows padded to a multiple of the stage height PC
     int r4, Gx, Gy, Wp, Hp;            // halo column origin step, ghost widths, padded sizes
     int BW;                            // stage box width: columns col0 - r4 .. col0 - r4 + BW - 1

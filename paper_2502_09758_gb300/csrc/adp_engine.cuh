@@ -50,6 +50,8 @@ __shared__ int g_sflag;
 // each warp's two mbarriers (outside the warp regions, which the FFT phases
 // reuse as one CTA-wide scratch area between passes)
 __shared__ __align__(8) uint64_t g_mbar[MAXNW_FFT][2];
+// the FFT phases' bulk copies: column stages 0 and 1, the row buffer
+__shared__ __align__(8) uint64_t g_fmbar[3];
 
 // Report of a MAID step, accumulated by thread 0 of each CTA (shared memory,
 // so that it occupies no registers while the solves run).
@@ -88,6 +90,8 @@ struct Eng {
     bool alive;                    // false once a grid barrier failed (uniform in the CTA)
     bool tmafail;                  // this warp gave up waiting for a TMA copy
     bool gedge;                    // the current strip has pixels whose copies live in the ghosts
+    unsigned fph, fpend;           // g_fmbar: parity of each barrier's next completion; copies issued, not waited
+    bool ffail;                    // a wait on g_fmbar gave up (uniform in the CTA)
 
     // the warp's region, derived from sb0 (Layout: two stages, two halo-1
     // tiles, an interior tile, the mbarriers)
@@ -115,7 +119,8 @@ struct Eng {
     __device__ int ns() const { return cx.Kp / PC; }
 
     __device__ Eng(const Ctx<T> &c, const Ctx<T> *maps, int nblk_, int bid_, unsigned char *smem)
-        : cx(c), mc(maps), mph(0), wslot(1), nblk(nblk_), bid(bid_), epoch(0), alive(true), tmafail(false), gedge(true)
+        : cx(c), mc(maps), mph(0), wslot(1), nblk(nblk_), bid(bid_), epoch(0), alive(true), tmafail(false), gedge(true),
+          fph(0), fpend(0), ffail(false)
     {
         lane = threadIdx.x & 31;
         warp = threadIdx.x >> 5;
@@ -127,6 +132,8 @@ struct Eng {
         if (lane == 0) {
             mbar_init(&mbar()[0], 1);
             mbar_init(&mbar()[1], 1);
+            if (kFFT && warp == 0)
+                for (int i = 0; i < 3; ++i) mbar_init(&g_fmbar[i], 1);
             fence_mbar_init();
         }
         __syncthreads();
@@ -259,8 +266,34 @@ struct Eng {
     // bounded wait for whatever copies a failed warp may still have in flight
     __device__ void drain()
     {
-        if (!tmafail) return;
-        for (int i = 0; i < 2; ++i) mbar_wait(&mbar()[i], (mph >> i) & 1u, cx.timeout_ns);
+        if (tmafail)
+            for (int i = 0; i < 2; ++i) mbar_wait(&mbar()[i], (mph >> i) & 1u, cx.timeout_ns);
+        if (ffail) fdrain();
+    }
+    // bounded wait for the FFT phases' bulk copies still in flight (every thread)
+    __device__ void fdrain()
+    {
+        for (int i = 0; i < 3; ++i)
+            if ((fpend >> i) & 1u) {
+                mbar_wait(&g_fmbar[i], (fph >> i) & 1u, cx.timeout_ns);
+                fph ^= 1u << i;
+            }
+        fpend = 0;
+    }
+    // every thread: wait (bounded) for the copies on g_fmbar[i]; CTA-uniform
+    // result.  On a timeout the status is raised and the CTA stops issuing
+    // (ffail); the next grid barrier then fails everywhere.
+    __device__ bool fland(int i)
+    {
+        const bool ok = __syncthreads_and(mbar_wait(&g_fmbar[i], (fph >> i) & 1u, cx.timeout_ns)) != 0;
+        if (!ok) {
+            if (tid() == 0) raise(ST_TIMEOUT);
+            ffail = true;
+            return false;
+        }
+        fph ^= 1u << i;
+        fpend &= ~(1u << i);
+        return true;
     }
 
     // lane 0: expect and issue stage k (buffer k & 1) of image img at tile row
@@ -680,11 +713,14 @@ struct Eng {
     __device__ static int sidx(int nu) { return nu + 2 * (nu >> 5); }
     __device__ int brevw(int v) const { return (int)(__brev((unsigned)v) >> (32 - cx.flogW)) & (cx.W - 1); }
 
-    // copies of row task t (rows i0 .. i0+2frp-1 of channel c), whole 16-byte
-    // copies: its half spectra into stage st, and the image rows i0-1 ..
-    // i0+2frp of buffer b1 followed by those of b2 (RF_HESS: again with the
-    // halo rows; RF_FISTA: the task's rows only, then those of c = B^T y_delta)
-    // into the row buffer
+    // copies of row task t (rows i0 .. i0+2frp-1 of channel c): its half
+    // spectra into stage st (16-byte cp.async, one group), and, by bulk
+    // copies on g_fmbar[2] (warp 0; called by every thread), the image rows
+    // i0-1 .. i0+2frp of buffer b1 followed by those of b2 (RF_HESS: again
+    // with the halo rows; RF_FISTA: the task's rows only, then those of
+    // c = B^T y_delta) into the row buffer.  Shared memory that generic code
+    // used must be released to the async proxy (fence_proxy_async_smem and a
+    // CTA barrier) before the bulk copies are issued.
     __device__ void rtask_spc(int t, float *st)
     {
         const int W2 = cx.W / 2, RP = cx.frp, tpc = cx.H / (2 * RP), bd = blockDim.x;
@@ -700,27 +736,25 @@ struct Eng {
     }
     __device__ void rtask_rows(int t, int mode, int b1, int b2)
     {
-        const int W = cx.W, RP = cx.frp, tpc = cx.H / (2 * RP), bd = blockDim.x, q = W >> 2;
+        fpend |= 4u;
+        if (warp != 0) return;
+        const int W = cx.W, RP = cx.frp, tpc = cx.H / (2 * RP);
         const int c = t / tpc, i0 = (t - c * tpc) * 2 * RP;
-        auto rows = [&](float *dst, int b, int r0, int nr) {
-            const T *src = buf(b) + c * cx.HWp + (long long)(r0 + cx.Gy) * cx.Wp + cx.Gx;
-            for (int e = tid(); e < nr * q; e += bd) {
-                const int r = e / q, k = e - r * q;
-                cp_async16(dst + r * W + 4 * k, src + (long long)r * cx.Wp + 4 * k);
-            }
-        };
+        const bool hess = mode == RF_HESS;
+        const int n1 = 2 * RP + 2, n2 = hess ? 2 * RP + 2 : 2 * RP, r2 = hess ? i0 - 1 : i0;
+        uint64_t *mb = &g_fmbar[2];
+        if (lane == 0) mbar_expect_tx(mb, (unsigned)((n1 + n2 + (hess ? 0 : 2 * RP)) * W) * 4u);
+        __syncwarp();
         float *rw = rrows();
-        rows(rw, b1, i0 - 1, 2 * RP + 2);
-        if (mode == RF_HESS) {
-            rows(rw + (2 * RP + 2) * W, b2, i0 - 1, 2 * RP + 2);
-        } else {
-            rows(rw + (2 * RP + 2) * W, b2, i0, 2 * RP);
-            // RF_FISTA: rows i0 .. i0+2frp-1 of c = B^T y_delta (dense, contiguous)
-            const float *cs = cx.fc + ((long long)c * cx.H + i0) * W;
-            float *cd = rw + (4 * RP + 2) * W;
-            for (int e = tid(); e < 2 * RP * q; e += bd) cp_async16(cd + 4 * e, cs + 4 * e);
+        for (int q = lane; q < n1 + n2; q += 32) {      // one bulk copy per padded row (its interior)
+            const bool first = q < n1;
+            const int row = first ? i0 - 1 + q : r2 + (q - n1);
+            const T *src = buf(first ? b1 : b2) + c * cx.HWp + (long long)(row + cx.Gy) * cx.Wp + cx.Gx;
+            bulk_load(rw + q * W, src, (unsigned)W * 4u, mb);
         }
-        cp_async_commit();
+        // RF_FISTA: rows i0 .. i0+2frp-1 of c = B^T y_delta (dense: one copy)
+        if (!hess && lane == 0)
+            bulk_load(rw + (4 * RP + 2) * W, cx.fc + ((long long)c * cx.H + i0) * W, (unsigned)(2 * RP * W) * 4u, mb);
     }
 
     // The row phase over all row tasks.  The inverse row transform starts from
@@ -764,11 +798,13 @@ struct Eng {
             // task's own spectrum, then its rows, at the task's start.  Either
             // way the groups complete in the order spectrum(t), rows(t), ...
             const bool dbl = cx.fnst > 1;
+            fence_proxy_async_smem();      // earlier phases' use of the scratch, before the copies into it
+            __syncthreads();
             if (inv && dbl && bid < ntask) {
                 rtask_spc(bid, rstage(0));
                 rtask_rows(bid, mode, b1, b2);
             }
-            for (int t = bid; t < ntask; t += nblk, ++u) {
+            for (int t = bid; t < ntask && !ffail; t += nblk, ++u) {
                 const int c = t / tpc, i0 = (t - c * tpc) * 2 * RP;
                 float *st = rstage(dbl ? (u & 1) : 0);
                 const bool nxt = dbl && t + nblk < ntask;
@@ -778,17 +814,13 @@ struct Eng {
                         rtask_rows(t, mode, b1, b2);
                     }
                     if (nxt) rtask_spc(t + nblk, rstage((u + 1) & 1));
-                    if (nxt) cp_async_wait<2>();
-                    else cp_async_wait<1>();
+                    if (nxt) cp_async_wait<1>();
+                    else cp_async_wait<0>();
                 }
                 __syncthreads();
                 const float2 *sp = reinterpret_cast<const float2 *>(st);
                 const float *rw = rrows();                          // rows i0-1 .. i0+2RP of b1, then b2's
-                auto rows_landed = [&]() {
-                    if (nxt) cp_async_wait<1>();
-                    else cp_async_wait<0>();
-                    __syncthreads();
-                };
+                auto rows_landed = [&]() { return fland(2); };
                 const float2 *zn = cx.fzn + (long long)c * H + i0;
                 // the packed spectrum at bit-reversed position e (first inverse pass)
                 auto ld_pack = [=](int sq, int e, int) {
@@ -821,7 +853,7 @@ struct Eng {
                         else fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_wa, nomid, st_wa);
                         __syncthreads();
                     }
-                    rows_landed();
+                    if (!rows_landed()) break;
                     // the per-pixel step in natural order, four consecutive
                     // pixels of both rows of a pair per thread: B^T B y_k from
                     // the inverse, - B^T y_delta, + alpha grad J(y_k);
@@ -878,6 +910,7 @@ struct Eng {
                     if (cx.reg == 0) pixels(std::integral_constant<int, 0>());
                     else if (cx.reg == 1) pixels(std::integral_constant<int, 1>());
                     else pixels(std::integral_constant<int, 2>());
+                    fence_proxy_async_smem();  // the row buffer's reads, before its refill
                     __syncthreads();
                     ghost_rows(O2, c, i0, 2 * RP, [&](int r, int j) {
                         const float2 z = wa[slot(r >> 1, j)];
@@ -890,55 +923,113 @@ struct Eng {
                     fft_pass_n<0>(lpass(np - 1), W, RP, lrp, cx.ftwW, spass(np - 1), ld_wa, nomid, st_wa);
                     __syncthreads();
                 } else if (mode == RF_HESS) {
-                    auto st_top = [&](int sq, int e, int, float2 v) {
-                        const int j = e, jl = (j - 1) & (W - 1), jr = (j + 1) & (W - 1);
-                        T ps2[2];
-#pragma unroll
-                        for (int pp = 0; pp < 2; ++pp) {
-                            const int r = 2 * sq + pp, i = i0 + r;
-                            const float *pm = rw + (r + 1) * W, *xm = pm + (2 * RP + 2) * W;
-                            const T xc = xm[j], pc = pm[j];
-                            const T wl = ddphi<T>(cx.reg, xc - xm[jl], g, ig);
-                            const T wr = ddphi<T>(cx.reg, xm[jr] - xc, g, ig);
-                            const T wu = ddphi<T>(cx.reg, xc - xm[j - W], g, ig);
-                            const T wd = ddphi<T>(cx.reg, xm[j + W] - xc, g, ig);
-                            const T th = wl * (pc - pm[jl]) - wr * (pm[jr] - pc) + wu * (pc - pm[j - W]) -
-                                         wd * (pm[j + W] - pc);
-                            const T hv = (pp ? v.y : v.x) * scale + al * th;
-                            put(O1, c, i, j, hv);
-                            ps2[pp] = hv * pc;
-                        }
-                        part = Sc::addv(part, ps2[0] + ps2[1]);
-                    };
                     for (int i = 0; i < np; ++i) {
-                        const bool top = i == np - 1;
-                        if (top) rows_landed();
-                        if (i == 0 && top) fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_pack, nomid, st_top);
-                        else if (i == 0) fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_pack, nomid, st_wa);
-                        else if (top) fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_wa, nomid, st_top);
+                        if (i == 0) fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_pack, nomid, st_wa);
                         else fft_pass_n<1>(lpass(i), W, RP, lrp, cx.ftwW, spass(i), ld_wa, nomid, st_wa);
                         __syncthreads();
                     }
-                    if (nxt) rtask_rows(t + nblk, mode, b1, b2);
+                    if (!rows_landed()) break;
+                    // the per-pixel step, four consecutive pixels of both rows
+                    // of a pair per thread: H p = B^T B p (from the inverse) +
+                    // alpha D^T(phi''(D x) . D p) to global memory (interior,
+                    // 16-byte stores; the work area keeps it for the ghost
+                    // copies), <p, H p>
+                    auto pixels = [&](auto regc) {
+                        constexpr int REG = decltype(regc)::value;
+                        const int lq = lw - 2, q4 = W >> 2;
+                        for (int e = tid(); e < RP * q4; e += bd) {
+                            const int sq = e >> lq, j0 = (e & (q4 - 1)) << 2;
+                            float2 z[4];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) z[q] = wa[slot(sq, j0 + q)];
+                            float ho[2][4];
+                            T ps = T(0);       // this thread's share of <p, H p> (FP32, then float-float)
+#pragma unroll
+                            for (int pp = 0; pp < 2; ++pp) {
+                                const int r = 2 * sq + pp;
+                                const float *pm = rw + (r + 1) * W, *xm = pm + (2 * RP + 2) * W;
+                                const float4 pc4 = *reinterpret_cast<const float4 *>(pm + j0);
+                                const float4 pu4 = *reinterpret_cast<const float4 *>(pm - W + j0);
+                                const float4 pd4 = *reinterpret_cast<const float4 *>(pm + W + j0);
+                                const float4 xc4 = *reinterpret_cast<const float4 *>(xm + j0);
+                                const float4 xu4 = *reinterpret_cast<const float4 *>(xm - W + j0);
+                                const float4 xd4 = *reinterpret_cast<const float4 *>(xm + W + j0);
+                                const float ps6[6] = {pm[(j0 - 1) & (W - 1)], pc4.x, pc4.y, pc4.z, pc4.w,
+                                                      pm[(j0 + 4) & (W - 1)]};
+                                const float xs6[6] = {xm[(j0 - 1) & (W - 1)], xc4.x, xc4.y, xc4.z, xc4.w,
+                                                      xm[(j0 + 4) & (W - 1)]};
+                                const float pu[4] = {pu4.x, pu4.y, pu4.z, pu4.w}, pd[4] = {pd4.x, pd4.y, pd4.z, pd4.w};
+                                const float xu[4] = {xu4.x, xu4.y, xu4.z, xu4.w}, xd[4] = {xd4.x, xd4.y, xd4.z, xd4.w};
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) {
+                                    const T xc = xs6[q + 1], pc = ps6[q + 1];
+                                    const T wl = ddphi<T>(REG, xc - xs6[q], g, ig);
+                                    const T wr = ddphi<T>(REG, xs6[q + 2] - xc, g, ig);
+                                    const T wu = ddphi<T>(REG, xc - xu[q], g, ig);
+                                    const T wd = ddphi<T>(REG, xd[q] - xc, g, ig);
+                                    const T th = wl * (pc - ps6[q]) - wr * (ps6[q + 2] - pc) + wu * (pc - pu[q]) -
+                                                 wd * (pd[q] - pc);
+                                    const T hv = (pp ? z[q].y : z[q].x) * scale + al * th;
+                                    ho[pp][q] = hv;
+                                    ps += hv * pc;
+                                }
+                                *reinterpret_cast<float4 *>(O1 + pidx(c, i0 + r, j0)) =
+                                    make_float4(ho[pp][0], ho[pp][1], ho[pp][2], ho[pp][3]);
+                            }
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) wa[slot(sq, j0 + q)] = make_float2(ho[0][q], ho[1][q]);
+                            part = Sc::addv(part, ps);
+                        }
+                    };
+                    if (cx.reg == 0) pixels(std::integral_constant<int, 0>());
+                    else if (cx.reg == 1) pixels(std::integral_constant<int, 1>());
+                    else pixels(std::integral_constant<int, 2>());
+                    fence_proxy_async_smem();  // the row buffer's reads, before its refill
+                    __syncthreads();
+                    if (nxt) rtask_rows(t + nblk, mode, b1, b2);   // the row buffer is free
+                    ghost_rows(O1, c, i0, 2 * RP, [&](int r, int j) {
+                        const float2 z = wa[slot(r >> 1, j)];
+                        return (r & 1) ? z.y : z.x;
+                    });
+                    __syncthreads();           // the work area is rewritten by the next task
                     continue;                  // no forward transform
                 } else {
-                    // RF_FWD / RF_CGP: the first forward pass loads the image rows
-                    auto ld_img = [&](int sq, int e, int) {
-                        float pv[2];
+                    // RF_FWD / RF_CGP: the image rows (RF_CGP: p = r + sc p_prev,
+                    // to global memory with its ghost copies) into the work
+                    // area in natural order, four consecutive pixels of both
+                    // rows of a pair per thread (16-byte loads)
+                    const int lq = lw - 2, q4 = W >> 2;
+                    for (int e = tid(); e < RP * q4; e += bd) {
+                        const int sq = e >> lq, j0 = (e & (q4 - 1)) << 2;
+                        float4 v[2];
 #pragma unroll
                         for (int pp = 0; pp < 2; ++pp) {
-                            const int i = i0 + 2 * sq + pp;
-                            const long long o = pidx(c, i, e);
-                            if (mode == RF_CGP) {
-                                pv[pp] = B2 ? __ldcg(B1 + o) + sc * __ldcg(B2 + o) : __ldcg(B1 + o);
-                                put(O1, c, i, e, pv[pp]);
-                            } else {
-                                pv[pp] = __ldcg(B1 + o);
+                            const int o = pidx(c, i0 + 2 * sq + pp, j0);
+                            v[pp] = __ldcg(reinterpret_cast<const float4 *>(B1 + o));
+                            if (mode == RF_CGP && B2) {
+                                const float4 w = __ldcg(reinterpret_cast<const float4 *>(B2 + o));
+                                v[pp] = make_float4(v[pp].x + sc * w.x, v[pp].y + sc * w.y, v[pp].z + sc * w.z,
+                                                    v[pp].w + sc * w.w);
                             }
                         }
-                        return make_float2(pv[0], pv[1]);
-                    };
-                    fft_pass_n<0>(lpass(np - 1), W, RP, lrp, cx.ftwW, spass(np - 1), ld_img, nomid, st_wa);
+                        if (mode == RF_CGP)
+#pragma unroll
+                            for (int pp = 0; pp < 2; ++pp)
+                                *reinterpret_cast<float4 *>(O1 + pidx(c, i0 + 2 * sq + pp, j0)) = v[pp];
+                        wa[slot(sq, j0)] = make_float2(v[0].x, v[1].x);
+                        wa[slot(sq, j0 + 1)] = make_float2(v[0].y, v[1].y);
+                        wa[slot(sq, j0 + 2)] = make_float2(v[0].z, v[1].z);
+                        wa[slot(sq, j0 + 3)] = make_float2(v[0].w, v[1].w);
+                    }
+                    __syncthreads();
+                    if (mode == RF_CGP) {
+                        ghost_rows(O1, c, i0, 2 * RP, [&](int r, int j) {
+                            const float2 z = wa[slot(r >> 1, j)];
+                            return (r & 1) ? z.y : z.x;
+                        });
+                        __syncthreads();       // the ghost copies have read the work area
+                    }
+                    fft_pass_n<0>(lpass(np - 1), W, RP, lrp, cx.ftwW, spass(np - 1), ld_wa, nomid, st_wa);
                     __syncthreads();
                 }
                 // the remaining forward passes, then separate the two rows'
@@ -963,9 +1054,11 @@ struct Eng {
                         znw[2 * sq + 1] = xv;
                     }
                 }
+                fence_proxy_async_smem();      // the row buffer's reads, before a refill at the next task's start
                 __syncthreads();               // the work area is rewritten by the next task
             }
             cp_async_wait<0>();
+            if (ffail) fdrain();
             fence_proxy_async_smem();      // before later phases' TMA copies into the same shared memory
         }
         return part;
@@ -974,96 +1067,108 @@ struct Eng {
     // column phase: fncs stages of the half spectra, then as many of the symbol
     __device__ float *csym(int k) const { return reinterpret_cast<float *>(cstage(cx.fncs)) + (long long)k * cx.fcstage; }
 
-    // stage column task t (block blk of channel c, or the column W/2 of
-    // channel t - C*nb) into column stage k: element (i, k) of the spectrum at
-    // fslot(k, i, cnt) (8-byte copies), the symbol |F(k)|^2 of its columns in
-    // the order of fsh / fsn (16-byte copies where whole)
+    // thread 0: copies of column task t (block blk of channel c, or the
+    // column W/2 of channel t - C*nb) into column stage k on g_fmbar[k]: the
+    // spectrum dense, element (i, kk) at i * cnt + kk (tensor boxes of fzh;
+    // one bulk copy for the column W/2), and the symbol |F(k)|^2 of its
+    // columns in the order of fsh / fsn (one bulk copy; the column W/2's
+    // only when whole 16-byte units, else the product reads fsn).  Called by
+    // every thread (the pending bits stay uniform).
     __device__ void ctask_issue(int t, int k)
     {
-        const int H = cx.H, W2 = cx.W / 2, CB = cx.fcb2, nb = W2 / CB, lcb = __ffs(CB) - 1, bd = blockDim.x;
+        fpend |= 1u << k;
+        if (tid() != 0) return;
+        const int H = cx.H, W2 = cx.W / 2, CB = cx.fcb2, nb = W2 / CB;
         float2 *a = cstage(k);
         float *sm = csym(k);
-        const float *sy;
-        int n;
+        uint64_t *mb = &g_fmbar[k];
         if (t < cx.C * nb) {
-            const int c = t / nb, blk = t - c * nb;
-            const float2 *z = cx.fzh + (long long)c * H * W2 + blk * CB;
-            for (int e = tid(); e < H * CB; e += bd) {
-                const int i = e >> lcb, kk = e & (CB - 1);
-                cp_async8(a + fslot(kk, i, CB), z + (long long)i * W2 + kk);
-            }
-            sy = cx.fsh + ((long long)c * nb + blk) * H * CB;
-            n = H * CB;
+            const int c = t / nb, blk = t - c * nb, BR = H < 256 ? H : 256;
+            mbar_expect_tx(mb, (unsigned)(H * CB) * 12u);
+            for (int r0 = 0; r0 < H; r0 += BR) tma_load_2d(a + r0 * CB, &mc->map_fz, 2 * blk * CB, c * H + r0, mb);
+            bulk_load(sm, cx.fsh + ((long long)c * nb + blk) * H * CB, (unsigned)(H * CB) * 4u, mb);
         } else {
-            const float2 *z = cx.fzn + (long long)(t - cx.C * nb) * H;
-            for (int i = tid(); i < H; i += bd) cp_async8(a + i, z + i);
-            sy = cx.fsn + (long long)(t - cx.C * nb) * H;
-            n = H;
+            const int c = t - cx.C * nb;
+            const bool whole = (H & 3) == 0;
+            mbar_expect_tx(mb, (unsigned)H * (whole ? 12u : 8u));
+            bulk_load(a, cx.fzn + (long long)c * H, (unsigned)H * 8u, mb);
+            if (whole) bulk_load(sm, cx.fsn + (long long)c * H, (unsigned)H * 4u, mb);
         }
-        if ((n & 3) == 0)
-            for (int e = 4 * tid(); e < n; e += 4 * bd) cp_async16(sm + e, sy + e);
-        else
-            for (int e = tid(); e < n; e += bd) cp_async4(sm + e, sy + e);
-        cp_async_commit();
     }
 
     // The column phase over the half spectra in fzh / fzn: forward column
     // transforms, the product with |F(k)|^2 (the symbol of B^T B, staged with
     // the task's spectrum) over the staged spectrum, inverse column
-    // transforms; the last inverse pass stores to global memory.
+    // transforms, the block back to fzh / fzn by bulk stores.  Double
+    // buffered: the next task's copies go out after this task's forward
+    // passes, once the store that last read their buffer has read it.
     __device__ void cols_r2c()
     {
         if constexpr (kFFT) {
             const int H = cx.H, lh = cx.flogH, W2 = cx.W / 2, CB = cx.fcb2, nb = W2 / CB;
             const int ntask = cx.C * nb + cx.C, np = fft_npass(lh), bd = blockDim.x;
+            const bool dbl = cx.fncs > 1;
             auto nomid = [](int, int, int, auto &) {};
+            fence_proxy_async_smem();  // earlier phases' use of the scratch, before the copies into it
+            __syncthreads();
             int u = 0;
             if (bid < ntask) ctask_issue(bid, 0);
-            for (int t = bid; t < ntask; t += nblk, ++u) {
-                const int sk = cx.fncs > 1 ? (u & 1) : 0;
+            for (int t = bid; t < ntask && !ffail; t += nblk, ++u) {
+                const int sk = dbl ? (u & 1) : 0;
+                if (!fland(sk)) break;
                 float2 *a = cstage(sk);
                 const float *sm = csym(sk);
                 const int tn = t + nblk;
-                if (cx.fncs == 1) {
-                    if (u > 0) ctask_issue(t, 0);
-                    cp_async_wait<0>();
-                } else if (tn < ntask) {
-                    ctask_issue(tn, (u + 1) & 1);
-                    cp_async_wait<1>();
-                } else {
-                    cp_async_wait<0>();
-                }
-                __syncthreads();
                 const bool nyq = t >= cx.C * nb;
                 const int cnt = nyq ? 1 : CB, lc = __ffs(cnt) - 1;
                 const int c = nyq ? t - cx.C * nb : t / nb, blk = nyq ? 0 : t - c * nb;
-                float2 *zg = nyq ? cx.fzn + (long long)c * H : cx.fzh + (long long)c * H * W2 + blk * CB;
-                const long long gst = nyq ? 1 : W2;
-                auto ld_a = [=](int sq, int e, int) { return a[fslot(sq, e, cnt)]; };
-                auto st_a = [=](int sq, int e, int, float2 v) { a[fslot(sq, e, cnt)] = v; };
-                auto st_g = [=](int sq, int e, int, float2 v) { zg[(long long)e * gst + sq] = v; };
+                auto ld_a = [=](int sq, int e, int) { return a[e * cnt + sq]; };
+                auto st_a = [=](int sq, int e, int, float2 v) { a[e * cnt + sq] = v; };
                 auto lpass = [&](int i) { return fft_pass_len(lh, i); };
                 auto spass = [&](int i) { return fft_pass_s0(lh, i); };
                 for (int i = np - 1; i >= 0; --i) {
                     fft_pass_n<0>(lpass(i), H, cnt, lc, cx.ftwH, spass(i), ld_a, nomid, st_a);
                     __syncthreads();
                 }
-                // element (mu, k) of the task: symbol at mu * cnt + k
+                if (dbl && tn < ntask) {
+                    if (tid() == 0) bulk_wait_read_all();
+                    ctask_issue(tn, (u + 1) & 1);
+                }
+                // element (mu, k) of the task at mu * cnt + k, here and in the symbol
+                const float *sg = cx.fsn + (long long)c * H;
+                const bool sglob = nyq && (H & 3) != 0;
                 for (int e = tid(); e < H * cnt; e += bd) {
-                    float2 &v = a[fslot(e & (cnt - 1), e >> lc, cnt)];
-                    const float m2 = sm[e];
-                    v = make_float2(v.x * m2, v.y * m2);
+                    const float m2 = sglob ? __ldcg(sg + e) : sm[e];
+                    a[e] = make_float2(a[e].x * m2, a[e].y * m2);
                 }
                 __syncthreads();
                 for (int i = 0; i < np; ++i) {
-                    if (i == np - 1) fft_pass_n<1>(lpass(i), H, cnt, lc, cx.ftwH, spass(i), ld_a, nomid, st_g);
-                    else fft_pass_n<1>(lpass(i), H, cnt, lc, cx.ftwH, spass(i), ld_a, nomid, st_a);
+                    fft_pass_n<1>(lpass(i), H, cnt, lc, cx.ftwH, spass(i), ld_a, nomid, st_a);
                     __syncthreads();
                 }
-                __syncthreads();           // the buffers are refilled two tasks later
+                fence_proxy_async_smem();  // the block's writes, before the bulk store reads them
+                __syncthreads();
+                if (tid() == 0) {
+                    if (nyq) {
+                        bulk_store(cx.fzn + (long long)c * H, a, (unsigned)H * 8u);
+                    } else {
+                        const int BR = H < 256 ? H : 256;
+                        for (int r0 = 0; r0 < H; r0 += BR) tma_store_2d(&mc->map_fz, 2 * blk * CB, c * H + r0, a + r0 * CB);
+                    }
+                    bulk_commit();
+                }
+                if (!dbl && tn < ntask) {
+                    if (tid() == 0) bulk_wait_read_all();
+                    ctask_issue(tn, 0);
+                }
             }
-            cp_async_wait<0>();
+            if (ffail) fdrain();
+            if (tid() == 0) {
+                bulk_wait_all();       // the stores are complete before the grid barrier
+                fence_proxy_async();
+            }
             fence_proxy_async_smem();
+            __syncthreads();
         }
     }
 
@@ -1827,30 +1932,41 @@ struct Eng {
             const T a = (T)Sc::to_elem(Sc::div(rr, php));
             S rn = Sc::zero();
             {
-                const T *PCr = buf(pc);
+                // 16-byte vectors: the padded pitch, the ghost width and W are
+                // multiples of 4, so a vector is wholly interior or wholly ghost
+                constexpr int V = 1;
+                const float4 *P4 = reinterpret_cast<const float4 *>(buf(pc));
+                const float4 *H4 = reinterpret_cast<const float4 *>(HP);
+                float4 *Q4 = reinterpret_cast<float4 *>(Q), *R4 = reinterpret_cast<float4 *>(R);
+                const int w4 = cx.Wp >> 2, g4 = cx.Gx >> 2, e4 = (cx.Gx + cx.W) >> 2;
                 for (int row = gw(); row < cx.C * cx.Hp; row += TW()) {
-                    const long long rb = (long long)row * cx.Wp;
+                    const long long rb = (long long)row * w4;
+                    const int pi = row % cx.Hp;
+                    const bool irow = pi >= cx.Gy && pi < cx.Gy + cx.H;
                     T s = T(0);
-                    for (int j0 = 0; j0 < cx.Wp; j0 += 32 * EWB) {
-                        T pv[EWB], qv[EWB], rv[EWB], hv[EWB];
+                    for (int j0 = lane; j0 < w4; j0 += 32 * V) {
+                        float4 pv[V], qv[V], rv[V], hv[V];
 #pragma unroll
-                        for (int u = 0; u < EWB; ++u) {
-                            const int j = j0 + u * 32 + lane;
-                            if (j < cx.Wp) {
-                                pv[u] = __ldcg(PCr + rb + j);
-                                qv[u] = __ldcg(Q + rb + j);
-                                rv[u] = __ldcg(R + rb + j);
-                                hv[u] = __ldcg(HP + rb + j);
+                        for (int u = 0; u < V; ++u) {
+                            const int j = j0 + u * 32;
+                            if (j < w4) {
+                                pv[u] = __ldcg(P4 + rb + j);
+                                qv[u] = __ldcg(Q4 + rb + j);
+                                rv[u] = __ldcg(R4 + rb + j);
+                                hv[u] = __ldcg(H4 + rb + j);
                             }
                         }
 #pragma unroll
-                        for (int u = 0; u < EWB; ++u) {
-                            const int j = j0 + u * 32 + lane;
-                            if (j < cx.Wp) {
-                                Q[rb + j] = qv[u] + a * pv[u];
-                                const T r2 = rv[u] - a * hv[u];
-                                R[rb + j] = r2;
-                                if (interior(row, j)) s += r2 * r2;
+                        for (int u = 0; u < V; ++u) {
+                            const int j = j0 + u * 32;
+                            if (j < w4) {
+                                Q4[rb + j] = make_float4(qv[u].x + a * pv[u].x, qv[u].y + a * pv[u].y,
+                                                         qv[u].z + a * pv[u].z, qv[u].w + a * pv[u].w);
+                                const float4 r2 = make_float4(rv[u].x - a * hv[u].x, rv[u].y - a * hv[u].y,
+                                                              rv[u].z - a * hv[u].z, rv[u].w - a * hv[u].w);
+                                R4[rb + j] = r2;
+                                if (irow && j >= g4 && j < e4)
+                                    s += (r2.x * r2.x + r2.y * r2.y) + (r2.z * r2.z + r2.w * r2.w);
                             }
                         }
                     }
