@@ -740,21 +740,27 @@ struct Eng {
         if (warp != 0) return;
         const int W = cx.W, RP = cx.frp, tpc = cx.H / (2 * RP);
         const int c = t / tpc, i0 = (t - c * tpc) * 2 * RP;
-        const bool hess = mode == RF_HESS;
-        const int n1 = 2 * RP + 2, n2 = hess ? 2 * RP + 2 : 2 * RP, r2 = hess ? i0 - 1 : i0;
+        // blocks of padded rows: n1 of b1 from r1, n2 of b2 from r2 (after the
+        // first block's 2 RP + 2 rows in the RF_FISTA / RF_HESS layout, after
+        // its 2 RP rows otherwise); RF_FISTA adds the 2 RP rows of c
+        const bool halo = mode == RF_FISTA || mode == RF_HESS;
+        const int n1 = halo ? 2 * RP + 2 : 2 * RP, r1 = halo ? i0 - 1 : i0;
+        const int n2 = mode == RF_HESS ? 2 * RP + 2 : (mode == RF_FWD || b2 < 0 ? 0 : 2 * RP);
+        const int r2 = mode == RF_HESS ? i0 - 1 : i0, o2 = halo ? 2 * RP + 2 : 2 * RP;
+        const int nc = mode == RF_FISTA ? 2 * RP : 0;
         uint64_t *mb = &g_fmbar[2];
-        if (lane == 0) mbar_expect_tx(mb, (unsigned)((n1 + n2 + (hess ? 0 : 2 * RP)) * W) * 4u);
+        if (lane == 0) mbar_expect_tx(mb, (unsigned)((n1 + n2 + nc) * W) * 4u);
         __syncwarp();
         float *rw = rrows();
         for (int q = lane; q < n1 + n2; q += 32) {      // one bulk copy per padded row (its interior)
             const bool first = q < n1;
-            const int row = first ? i0 - 1 + q : r2 + (q - n1);
+            const int row = first ? r1 + q : r2 + (q - n1);
             const T *src = buf(first ? b1 : b2) + c * cx.HWp + (long long)(row + cx.Gy) * cx.Wp + cx.Gx;
-            bulk_load(rw + q * W, src, (unsigned)W * 4u, mb);
+            bulk_load(rw + (first ? q : o2 + (q - n1)) * W, src, (unsigned)W * 4u, mb);
         }
         // RF_FISTA: rows i0 .. i0+2frp-1 of c = B^T y_delta (dense: one copy)
-        if (!hess && lane == 0)
-            bulk_load(rw + (4 * RP + 2) * W, cx.fc + ((long long)c * cx.H + i0) * W, (unsigned)(2 * RP * W) * 4u, mb);
+        if (nc && lane == 0)
+            bulk_load(rw + (4 * RP + 2) * W, cx.fc + ((long long)c * cx.H + i0) * W, (unsigned)(nc * W) * 4u, mb);
     }
 
     // The row phase over all row tasks.  The inverse row transform starts from
@@ -800,19 +806,19 @@ struct Eng {
             const bool dbl = cx.fnst > 1;
             fence_proxy_async_smem();      // earlier phases' use of the scratch, before the copies into it
             __syncthreads();
-            if (inv && dbl && bid < ntask) {
-                rtask_spc(bid, rstage(0));
+            if (dbl && bid < ntask) {
+                if (inv) rtask_spc(bid, rstage(0));
                 rtask_rows(bid, mode, b1, b2);
             }
             for (int t = bid; t < ntask && !ffail; t += nblk, ++u) {
                 const int c = t / tpc, i0 = (t - c * tpc) * 2 * RP;
                 float *st = rstage(dbl ? (u & 1) : 0);
                 const bool nxt = dbl && t + nblk < ntask;
+                if (!dbl) {
+                    if (inv) rtask_spc(t, st);
+                    rtask_rows(t, mode, b1, b2);
+                }
                 if (inv) {
-                    if (!dbl) {
-                        rtask_spc(t, st);
-                        rtask_rows(t, mode, b1, b2);
-                    }
                     if (nxt) rtask_spc(t + nblk, rstage((u + 1) & 1));
                     if (nxt) cp_async_wait<1>();
                     else cp_async_wait<0>();
@@ -994,34 +1000,35 @@ struct Eng {
                     __syncthreads();           // the work area is rewritten by the next task
                     continue;                  // no forward transform
                 } else {
-                    // RF_FWD / RF_CGP: the image rows (RF_CGP: p = r + sc p_prev,
-                    // to global memory with its ghost copies) into the work
-                    // area in natural order, four consecutive pixels of both
-                    // rows of a pair per thread (16-byte loads)
+                    // RF_FWD / RF_CGP: the staged image rows (RF_CGP: p = r + sc
+                    // p_prev, to global memory with its ghost copies) into the
+                    // work area in natural order, four consecutive pixels of
+                    // both rows of a pair per thread
+                    if (!rows_landed()) break;
                     const int lq = lw - 2, q4 = W >> 2;
+                    const bool two = mode == RF_CGP && B2;
                     for (int e = tid(); e < RP * q4; e += bd) {
                         const int sq = e >> lq, j0 = (e & (q4 - 1)) << 2;
                         float4 v[2];
 #pragma unroll
                         for (int pp = 0; pp < 2; ++pp) {
-                            const int o = pidx(c, i0 + 2 * sq + pp, j0);
-                            v[pp] = __ldcg(reinterpret_cast<const float4 *>(B1 + o));
-                            if (mode == RF_CGP && B2) {
-                                const float4 w = __ldcg(reinterpret_cast<const float4 *>(B2 + o));
+                            const int r = 2 * sq + pp;
+                            v[pp] = *reinterpret_cast<const float4 *>(rw + r * W + j0);
+                            if (two) {
+                                const float4 w = *reinterpret_cast<const float4 *>(rw + (2 * RP + r) * W + j0);
                                 v[pp] = make_float4(v[pp].x + sc * w.x, v[pp].y + sc * w.y, v[pp].z + sc * w.z,
                                                     v[pp].w + sc * w.w);
                             }
+                            if (mode == RF_CGP) *reinterpret_cast<float4 *>(O1 + pidx(c, i0 + r, j0)) = v[pp];
                         }
-                        if (mode == RF_CGP)
-#pragma unroll
-                            for (int pp = 0; pp < 2; ++pp)
-                                *reinterpret_cast<float4 *>(O1 + pidx(c, i0 + 2 * sq + pp, j0)) = v[pp];
                         wa[slot(sq, j0)] = make_float2(v[0].x, v[1].x);
                         wa[slot(sq, j0 + 1)] = make_float2(v[0].y, v[1].y);
                         wa[slot(sq, j0 + 2)] = make_float2(v[0].z, v[1].z);
                         wa[slot(sq, j0 + 3)] = make_float2(v[0].w, v[1].w);
                     }
+                    fence_proxy_async_smem();  // the row buffer's reads, before its refill
                     __syncthreads();
+                    if (nxt) rtask_rows(t + nblk, mode, b1, b2);   // under the forward passes
                     if (mode == RF_CGP) {
                         ghost_rows(O1, c, i0, 2 * RP, [&](int r, int j) {
                             const float2 z = wa[slot(r >> 1, j)];
