@@ -18,6 +18,12 @@ Recipe (all draws from ``numpy.random.default_rng(seed)``):
   splatting, normalised; optional positive perturbation.
 * observation: ``y = b_true (*) x + N(0, sigma^2)`` with periodic boundary,
   formed in float64 through NumPy's FFT (data synthesis only).
+* 1D signal (Sec. 4.1's setting): length n, zero background with
+  ``max(3, n // 32)`` boxes (uniform start, length U{n/32 .. n/8}, height
+  U[0.2, 1]) and ``max(2, n // 64)`` single spikes (height U[0.3, 1]), painted
+  in order; the forward matrix A is the Gaussian convolution with sigma = 5,
+  the kernel cut at +-3 sigma and normalised to sum 1, zero outside the
+  signal; ``y = A x + N(0, 0.005^2)``; the learned operator starts at B_0 = A.
 """
 from __future__ import annotations
 
@@ -234,3 +240,51 @@ WORKLOADS = {
     "paper2d_motion": paper2d_motion,
     "paper2d_semiblind": paper2d_semiblind,
 }
+
+
+@dataclass
+class Signal1D:
+    """A 1D deconvolution instance: the forward matrix A (also B_0), the signal
+    and its noisy blurred observation."""
+    name: str
+    A: np.ndarray
+    x_true: np.ndarray
+    y: np.ndarray
+    params: dict = field(default_factory=dict)
+
+    @property
+    def n(self):
+        return self.x_true.shape[0]
+
+
+def gaussian_conv_matrix(n, sigma=5.0, cut=3.0):
+    """A[t, tau] = k(t - tau) for the Gaussian k of std sigma on |d| <= cut
+    sigma, normalised to sum 1; zero outside the signal."""
+    r = int(np.ceil(cut * sigma))
+    d = np.arange(-r, r + 1, dtype=np.float64)
+    k = np.exp(-0.5 * (d / sigma) ** 2)
+    k /= k.sum()
+    A = np.zeros((n, n))
+    t = np.arange(n)
+    for j, dd in enumerate(range(-r, r + 1)):
+        tau = t - dd
+        ok = (tau >= 0) & (tau < n)
+        A[t[ok], tau[ok]] = k[j]
+    return A
+
+
+def signal1d(n=256, seed=0, noise=5e-3, sigma=5.0):
+    """Sec. 4.1's 1D setting on a synthetic sparse, piecewise-constant signal
+    (the paper's own signal is not available): elastic net with
+    a1 = 1.2e-3, a2 = 4e-3, proximal-gradient step 0.1, beta = 0."""
+    rng = np.random.default_rng(30_000 + seed)
+    x = np.zeros(n)
+    for _ in range(max(3, n // 32)):
+        L = int(rng.integers(max(1, n // 32), max(2, n // 8) + 1))
+        s0 = int(rng.integers(0, max(1, n - L)))
+        x[s0:s0 + L] = rng.uniform(0.2, 1.0)
+    for _ in range(max(2, n // 64)):
+        x[int(rng.integers(0, n))] = rng.uniform(0.3, 1.0)
+    A = gaussian_conv_matrix(n, sigma)
+    y = A @ x + noise * rng.standard_normal(n)
+    return Signal1D(f"signal1d_n{n}", A, x, y, dict(a1=1.2e-3, a2=4e-3, lam=0.1, noise=noise))
