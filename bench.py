@@ -858,6 +858,147 @@ def run_batch64(args):
     print(json.dumps(line), flush=True)
 
 
+def run_en1d(args):
+    """Sec. 4.1's 1D elastic-net setting (synthetic sparse signal, n = 256,
+    Gaussian blur sigma 5 as a full matrix, a1 = 1.2e-3, a2 = 4e-3, proximal
+    step 0.1, beta = 0) from the paper's start (eps0 = delta0 = 1e-2,
+    alpha0 = 0.1; 300 lower-level iterations) to the stop rule eps <= 1e-4.
+    One step is one MAID run: one cluster launch runs every upper iteration
+    (adp_en1d_maid_run).  Beside it: one launch per upper iteration, and the
+    FP64 oracle on one host core running the same whole run.  Prints one JSON
+    line."""
+    import numpy as np
+    import torch
+    from paper_2502_09758_gb300 import adp, synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    inst = synth.signal1d(256, seed=0)
+    n = inst.n
+    A = torch.tensor(inst.A, dtype=torch.float32, device=dev)
+    y = torch.tensor(inst.y, dtype=torch.float32, device=dev)
+    pr = adp.En1d(A, y, a1=1.2e-3, a2=4e-3, lam=0.1)
+    over = dict(eps=1e-2, delta=1e-2, step=0.1, eps_stop=1e-4)
+    max_up = 50
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+
+    def psnr(x):
+        return float(10 * np.log10(1.0 / np.mean((x.detach().cpu().numpy().astype(np.float64) - inst.x_true) ** 2)))
+
+    def one_run():
+        s = pr.maid_init(**over)
+        B, x = A.clone(), y.clone()
+        steps = pr.maid_run(s, B, x, max_up)
+        return s, B, x, steps
+
+    for _ in range(max(args.warmup, 3)):
+        one_run()
+    props = torch.cuda.get_device_properties(dev)
+    clk = Clocks(str(getattr(props, "uuid", "")) or None)
+    torch.cuda.synchronize()
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms, iters = [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        s = pr.maid_init(**over)
+        B, x = A.clone(), y.clone()
+        torch.cuda.synchronize()
+        ev0.record()
+        steps = pr.maid_run(s, B, x, max_up)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+    clocks = clk.stop()
+    # the run's iteration totals (a host-stepped copy of the same run)
+    s1 = pr.maid_init(**over)
+    B1, x1 = A.clone(), y.clone()
+    tot_ll = tot_cg = ups = acc = 0
+    t0 = time.perf_counter()
+    for _ in range(max_up):
+        a_ = pr.maid_step(s1, B1, x1)
+        tot_ll += s1.ll_iters
+        tot_cg += s1.cg_iters
+        ups += 1
+        acc += int(a_)
+        if not a_ or s1.stopped:
+            break
+    torch.cuda.synchronize()
+    stepped_ms = (time.perf_counter() - t0) * 1e3
+    iters = tot_ll + tot_cg
+    run_ms = float(np.median(ms))
+    # e2e: host B0, x0 in, B, x, loss out, per run
+    Bh, yh = torch.empty((n, n), pin_memory=True), torch.empty(n, pin_memory=True)
+    Bh.copy_(A.cpu())
+    yh.copy_(y.cpu())
+    e2e = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B = Bh.to(dev, non_blocking=True)
+        x = yh.to(dev, non_blocking=True)
+        s = pr.maid_init(**over)
+        pr.maid_run(s, B, x, max_up)
+        Bo, xo = B.cpu(), x.cpu()
+        _ = float(s.loss)
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    # one lower-level iteration alone: launches of 20 and 220 proximal-gradient updates
+    tl = {}
+    for k in (20, 220, 20, 220):
+        xx = y.clone()
+        torch.cuda.synchronize()
+        ev0.record()
+        pr.lower_solve(A, xx, 0.0, k)
+        ev1.record()
+        torch.cuda.synchronize()
+        tl[k] = ev0.elapsed_time(ev1)
+    it_us = (tl[220] - tl[20]) / 200 * 1e3
+    flops_it = 4.0 * n * n                              # B x and B^T r: 2 n^2 flops each
+    pk = peaks()
+    peak_tf = SM_COUNT * FP32_LANES * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle.en1d as oen
+        P = oen.Problem(inst.A.astype(np.float32).astype(np.float64), inst.y.astype(np.float32).astype(np.float64))
+        so = P.maid_init(**over)
+        Bo_, xo_ = P.A.copy(), P.y.copy()
+        t0 = time.perf_counter()
+        oit = 0
+        for _ in range(max_up):
+            a_ = P.maid_step(so, Bo_, xo_)
+            oit += so.ll_iters + so.cg_iters
+            if not a_ or so.stopped:
+                break
+        osec = time.perf_counter() - t0
+        cpu = {"value": n * oit / osec / 1e6, "unit": "Mvalue·iter/s", "cores": 1, "kind": "oracle",
+               "sample": f"the whole MAID run to the stop rule on the FP64 NumPy oracle ({osec:.2f} s, "
+                         f"{oit} iterations)", "time_to_tolerance_s": osec}
+    line = {"metric": METRIC, "value": n * iters / (run_ms / 1e3) / 1e6, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": run_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "signal1d_n256_elastic_net", "n": n, "a1": 1.2e-3, "a2": 4e-3, "lam": 0.1,
+                       "beta": 0.0, "maid_eps0": 1e-2, "maid_step0": 0.1, "eps_stop": 1e-4, "ll_max_iters": 300,
+                       "step": "one MAID run to the stop rule", "l2": "flushed between timed runs (256 MB write)",
+                       "parallelism": "one 8-CTA cluster"},
+            "maid": {"time_to_tolerance_s": run_ms / 1e3, "form": "one cluster launch runs all upper iterations",
+                     "one_launch_per_upper_iteration_s": stepped_ms / 1e3, "upper_iters_per_run": ups,
+                     "accepted_per_run": acc, "prox_grad_iters": tot_ll, "cg_iters": tot_cg,
+                     "eps_end": s1.eps, "stopped": bool(s1.stopped), "final_loss": s1.loss,
+                     "final_psnr_x_db": psnr(x1), "psnr_y_db": float(10 * np.log10(1.0 / np.mean((inst.y - inst.x_true) ** 2)))},
+            "roofline": {"bound": "alu", "achieved": flops_it / (it_us * 1e-6) / 1e12, "peak": peak_tf,
+                         "unit": "TFLOP/s", "frac": flops_it / (it_us * 1e-6) / 1e12 / peak_tf, "traffic": None,
+                         "kernel": "en1d_kernel (8-CTA cluster, one proximal-gradient iteration)",
+                         "iteration_us": it_us,
+                         "flops_basis": "4 n^2 per iteration (B x and B^T r), event-timed launches of 20 and 220 "
+                                        "iterations; the peak is the whole GPU's FP32 rate"},
+            "e2e": {"value": n * iters / (float(np.median(e2e)) / 1e3) / 1e6, "unit": UNIT,
+                    "h2d_bytes_per_step": (n * n + n) * 4, "d2h_bytes_per_step": (n * n + n) * 4 + 8},
+            "gpu_launches": 1, "clocks": clocks}
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
 def run_bf16_operator(args):
     """B x with BF16 operands on the tensor cores against the FP32 operator
     on the CUDA cores, on 3 x 2048 x 2048 with K = 31 (the largest kernel the
@@ -957,10 +1098,10 @@ def main():
     ap.add_argument("--no-torch-baseline", action="store_true",
                     help="skip the MAID written with PyTorch tensor ops (reported beside the run)")
     ap.add_argument("--workload", default="rgb2048_k63",
-                    choices=list(WORKLOAD_SPECS) + ["batch64", "bf16_operator"],
+                    choices=list(WORKLOAD_SPECS) + ["batch64", "bf16_operator", "en1d"],
                     help="rgb2048_k63 (default) is the headline line; the others measure the other workloads: "
                          "batch64 the 64-problem batch, batched vs one at a time; bf16_operator the "
-                         "tensor-core operator against the FP32 one")
+                         "tensor-core operator against the FP32 one; en1d the 1D elastic-net setting")
     ap.add_argument("--profile-iters", type=int, default=4)
     ap.add_argument("--profile-case", default=None, choices=["rgb256_k15_motion", "rgb512_k31_gauss_perturbed",
                                                               "rgb2048_k63_motion_gauss"],
@@ -974,6 +1115,9 @@ def main():
         return
     if args.workload == "bf16_operator":
         run_bf16_operator(args)
+        return
+    if args.workload == "en1d":
+        run_en1d(args)
         return
     global EPS_STOP, MAX_UPPER, EPS0, STEP0
     spec = WORKLOAD_SPECS[args.workload]

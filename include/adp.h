@@ -316,6 +316,70 @@ double adp_last_kernel_ms(adp_problem *p);
 adp_status adp_lower_solve_noalloc(const adp_params *params, const void *y, const void *b, void *x, double eps,
                                    int max_iters, void *stream, int *iters, double *gradnorm);
 
+/* ------------------------------------------------------------------------
+ * 1D elastic-net variant (Sec. 4.1).  The operator is a full n x n matrix B
+ * (the kernel b(t, tau) of Eq. 2.4 sampled on the signal's grid), learned with
+ * beta = 0, so the upper level is l(B) = ||A x(B) - y||^2 (Eq. 2.5a) and the
+ * lower level is h(x; B) = 1/2 ||B x - y||^2 + a1 ||x||_1 + a2 ||x||_2^2,
+ * solved by proximal gradient with step lam (Sec. 4.1).  The accuracy of a
+ * lower-level iterate is the norm of the proximal-gradient mapping
+ * G(x) = (x - prox(x - lam B^T (B x - y))) / lam; the hypergradient solves the
+ * Hessian system on the support S = {i : x_i != 0} of x by CG and is the
+ * rank-two matrix z = -((B x - y) q^T + (B q) x^T) (Algorithm 1).
+ *
+ * Every call runs on one thread-block cluster of 8 CTAs: each CTA holds 1/8 of
+ * B's rows and 1/8 of its columns in shared memory and the CTAs exchange
+ * vector slices through distributed shared memory.  FP32 matrices and
+ * vectors; dot products, norms and the line-search test in FP64.  Matrices
+ * are row-major n x n FP32 device arrays, vectors n FP32 device arrays, all
+ * owned by the caller; calls are ordered on the problem's stream and wait for
+ * it before returning their scalar outputs.  Errors: ADP_EINVAL for bad
+ * arguments (n not a multiple of 8 or above ADP_EN1D_MAX_N, null pointers,
+ * a1, a2 < 0, lam <= 0), ADP_ENOMEM / ADP_ECUDA as for the 2D problem. */
+#define ADP_EN1D_MAX_N 384
+typedef struct {
+    int n;              /* signal length, a multiple of 8, 8 .. ADP_EN1D_MAX_N   */
+    double a1, a2;      /* elastic net a1 ||x||_1 + a2 ||x||_2^2 (1.2e-3, 4e-3)  */
+    double lam;         /* proximal-gradient step (0.1)                         */
+} adp_en1d_params;
+typedef struct adp_en1d adp_en1d;
+
+/* A: the forward matrix (n x n), y: the data (n); both device pointers, read
+ * by every later call (the caller keeps them alive).  stream: a cudaStream_t
+ * or NULL. */
+adp_status adp_en1d_create(const adp_en1d_params *params, const float *A, const float *y, void *stream,
+                           adp_en1d **out);
+void adp_en1d_destroy(adp_en1d *p);
+
+/* Proximal gradient from x (in: warm start, out: the result) for the
+ * operator B: returns the first iterate with ||G|| <= eps, or the iterate
+ * after max_iters updates; iters = updates made, gmap_norm = its ||G||. */
+adp_status adp_en1d_lower_solve(adp_en1d *p, const float *B, float *x, double eps, int max_iters, int *iters,
+                                double *gmap_norm);
+
+/* l = ||A x - y||^2 and ||grad g(x)|| = ||2 A^T (A x - y)||. */
+adp_status adp_en1d_upper_loss(adp_en1d *p, const float *x, double *loss, double *gradx_norm);
+
+/* Algorithm 1, steps 2-3, on the support of x: CG from q = 0 on
+ * (B^T B + 2 a2 I)_SS q_S = grad g(x)_S until ||r|| <= delta or max_iters
+ * iterations, q = 0 off S; then z = -((B x - y) q^T + (B q) x^T).  q: n,
+ * z: n x n, both written. */
+adp_status adp_en1d_hypergrad(adp_en1d *p, const float *B, const float *x, double delta, int max_iters, float *q,
+                              float *z, int *cg_iters, double *resnorm);
+
+/* Algorithm 2 with Sec. 4.1's constants: adp_en1d_maid_init fills s (eps =
+ * delta = 1e-2, alpha = 0.1, the 2D problem's line-search constants, 300
+ * lower-level iterations, L_gx = 2 ||A||_1 ||A||_inf).  adp_en1d_maid_step
+ * runs one upper iteration in one cluster launch and updates B and x in
+ * place on acceptance (the same report fields as adp_maid_step; a step that
+ * exhausts its rounds or meets the stop rule leaves B and x as they were).
+ * adp_en1d_maid_run runs up to max_steps upper iterations in one launch,
+ * ending early when the stop rule fires or a step exhausts its rounds;
+ * steps = upper iterations run. */
+adp_status adp_en1d_maid_init(adp_en1d *p, adp_maid_state *s);
+adp_status adp_en1d_maid_step(adp_en1d *p, adp_maid_state *s, float *B, float *x);
+adp_status adp_en1d_maid_run(adp_en1d *p, adp_maid_state *s, float *B, float *x, int max_steps, int *steps);
+
 /* Diagnostic of the failure path (no counterpart in the paper): one launch
  * of p's kernel in which CTA 0 never arrives at a grid barrier, so the bounded
  * wait of every other CTA runs out after the problem's wait_timeout_s.  The

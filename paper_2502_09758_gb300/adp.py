@@ -33,7 +33,9 @@ EXPORTS = ("adp_problem_create", "adp_problem_destroy", "adp_apply_B", "adp_appl
            "adp_grid_size", "adp_warps_per_cta", "adp_last_kernel_ms", "adp_trace_enable",
            "adp_trace_read", "adp_lower_solve_noalloc", "adp_selftest_wait_timeout", "adp_batch_create",
            "adp_batch_destroy", "adp_batch_maid_step", "adp_batch_maid_run_graph", "adp_batch_group_size",
-           "adp_batch_last_kernel_ms", "adp_last_error", "adp_status_string")
+           "adp_batch_last_kernel_ms", "adp_last_error", "adp_status_string",
+           "adp_en1d_create", "adp_en1d_destroy", "adp_en1d_lower_solve", "adp_en1d_upper_loss",
+           "adp_en1d_hypergrad", "adp_en1d_maid_init", "adp_en1d_maid_step", "adp_en1d_maid_run")
 
 
 class AdpError(RuntimeError):
@@ -47,6 +49,10 @@ class adp_params(ct.Structure):
                 ("alpha", ct.c_double), ("reg_param", ct.c_double), ("reg", ct.c_int),
                 ("beta", ct.c_double), ("sobolev_w0", ct.c_double), ("prec", ct.c_int),
                 ("wait_timeout_s", ct.c_double)]
+
+
+class adp_en1d_params(ct.Structure):
+    _fields_ = [("n", ct.c_int), ("a1", ct.c_double), ("a2", ct.c_double), ("lam", ct.c_double)]
 
 
 class adp_maid_state(ct.Structure):
@@ -116,6 +122,14 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
             "adp_batch_last_kernel_ms": (ct.c_double, [P]),
             "adp_last_error": (ct.c_char_p, []),
             "adp_status_string": (ct.c_char_p, [i]),
+            "adp_en1d_create": (i, [ct.POINTER(adp_en1d_params), vp, vp, vp, ct.POINTER(ct.c_void_p)]),
+            "adp_en1d_destroy": (None, [P]),
+            "adp_en1d_lower_solve": (i, [P, vp, vp, d, i, ip, dp]),
+            "adp_en1d_upper_loss": (i, [P, vp, dp, dp]),
+            "adp_en1d_hypergrad": (i, [P, vp, vp, d, i, vp, vp, ip, dp]),
+            "adp_en1d_maid_init": (i, [P, ct.POINTER(adp_maid_state)]),
+            "adp_en1d_maid_step": (i, [P, ct.POINTER(adp_maid_state), vp, vp]),
+            "adp_en1d_maid_run": (i, [P, ct.POINTER(adp_maid_state), vp, vp, i, ip]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -457,6 +471,86 @@ class Batch:
 
 
 # ----------------------------------------------------------------- autograd
+class En1d:
+    """The 1D elastic-net variant of Sec. 4.1 on one GPU: the forward matrix
+    A (n x n) and the data y (n), FP32 CUDA tensors; the learned operator B is
+    a full n x n matrix passed to each call."""
+
+    def __init__(self, A: torch.Tensor, y: torch.Tensor, a1=1.2e-3, a2=4e-3, lam=0.1, stream=None):
+        n = y.shape[0]
+        self.n, self.device = n, y.device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(y.device)
+        self.lib = load_library()
+        self._A, self._y = A, y          # the library reads them at every call
+        prm = adp_en1d_params(n, a1, a2, lam)
+        h = ct.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.adp_en1d_create(ct.byref(prm), _ptr(A, (n, n), torch.float32, "A"),
+                                            _ptr(y, (n,), torch.float32, "y"),
+                                            ct.c_void_p(self.stream.cuda_stream), ct.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle is not None:
+            self.lib.adp_en1d_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _m(self, t, name):
+        return _ptr(t, (self.n, self.n), torch.float32, name)
+
+    def _v(self, t, name):
+        return _ptr(t, (self.n,), torch.float32, name)
+
+    def lower_solve(self, B, x, eps, max_iters=300):
+        """x in/out; returns (updates, ||G||)."""
+        it, gn = ct.c_int(), ct.c_double()
+        with torch.cuda.device(self.device):
+            _check(self.lib.adp_en1d_lower_solve(self.handle, self._m(B, "B"), self._v(x, "x"), eps, max_iters,
+                                                 ct.byref(it), ct.byref(gn)))
+        return it.value, gn.value
+
+    def upper_loss(self, x):
+        l, g = ct.c_double(), ct.c_double()
+        with torch.cuda.device(self.device):
+            _check(self.lib.adp_en1d_upper_loss(self.handle, self._v(x, "x"), ct.byref(l), ct.byref(g)))
+        return l.value, g.value
+
+    def hypergrad(self, B, x, delta, max_iters=1000):
+        """Returns (z, q, CG iterations, ||r||)."""
+        q = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        z = torch.empty((self.n, self.n), dtype=torch.float32, device=self.device)
+        it, res = ct.c_int(), ct.c_double()
+        with torch.cuda.device(self.device):
+            _check(self.lib.adp_en1d_hypergrad(self.handle, self._m(B, "B"), self._v(x, "x"), delta, max_iters,
+                                               self._v(q, "q"), self._m(z, "z"), ct.byref(it), ct.byref(res)))
+        return z, q, it.value, res.value
+
+    def maid_init(self, **overrides) -> adp_maid_state:
+        s = adp_maid_state()
+        _check(self.lib.adp_en1d_maid_init(self.handle, ct.byref(s)))
+        for k, v in overrides.items():
+            setattr(s, k, v)
+        return s
+
+    def maid_step(self, s, B, x) -> bool:
+        with torch.cuda.device(self.device):
+            _check(self.lib.adp_en1d_maid_step(self.handle, ct.byref(s), self._m(B, "B"), self._v(x, "x")))
+        return bool(s.accepted)
+
+    def maid_run(self, s, B, x, max_steps):
+        steps = ct.c_int()
+        with torch.cuda.device(self.device):
+            _check(self.lib.adp_en1d_maid_run(self.handle, ct.byref(s), self._m(B, "B"), self._v(x, "x"),
+                                              max_steps, ct.byref(steps)))
+        return steps.value
+
+
 class ADPLower(torch.autograd.Function):
     """x~(b): the lower-level solution as a differentiable function of the kernel.
 

@@ -15,7 +15,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libadp.so")
-SOURCES = ["adp.cu", "adp_f32.cu", "adp_f64.cu", "adp_f32b.cu", "adp_f64b.cu", "adp_noalloc.cu", "adp_tc.cu", "adp_f32fft.cu"]
+SOURCES = ["adp.cu", "adp_f32.cu", "adp_f64.cu", "adp_f32b.cu", "adp_f64b.cu", "adp_noalloc.cu", "adp_tc.cu", "adp_f32fft.cu",
+           "adp_en1d.cu"]
 HEADERS = ["adp_device.cuh", "adp_engine.cuh", "adp_tc.cuh", "adp_fft.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
