@@ -327,18 +327,19 @@ adp_status adp_lower_solve_noalloc(const adp_params *params, const void *y, cons
  * Hessian system on the support S = {i : x_i != 0} of x by CG and is the
  * rank-two matrix z = -((B x - y) q^T + (B q) x^T) (Algorithm 1).
  *
- * Every call runs on one thread-block cluster of 8 CTAs: each CTA holds 1/8 of
- * B's rows and 1/8 of its columns in shared memory and the CTAs exchange
- * vector slices through distributed shared memory.  FP32 matrices and
+ * Every call runs on one thread-block cluster of 8 CTAs: for each operator it
+ * solves with, each CTA forms 1/8 of the rows of B^T B and B^T y in shared
+ * memory, and the CTAs exchange vector slices through distributed shared
+ * memory.  FP32 matrices and
  * vectors; dot products, norms and the line-search test in FP64.  Matrices
  * are row-major n x n FP32 device arrays, vectors n FP32 device arrays, all
  * owned by the caller; calls are ordered on the problem's stream and wait for
  * it before returning their scalar outputs.  Errors: ADP_EINVAL for bad
- * arguments (n not a multiple of 8 or above ADP_EN1D_MAX_N, null pointers,
+ * arguments (n not a multiple of 32 or above ADP_EN1D_MAX_N, null pointers,
  * a1, a2 < 0, lam <= 0), ADP_ENOMEM / ADP_ECUDA as for the 2D problem. */
 #define ADP_EN1D_MAX_N 384
 typedef struct {
-    int n;              /* signal length, a multiple of 8, 8 .. ADP_EN1D_MAX_N   */
+    int n;              /* signal length, a multiple of 32, 32 .. ADP_EN1D_MAX_N */
     double a1, a2;      /* elastic net a1 ||x||_1 + a2 ||x||_2^2 (1.2e-3, 4e-3)  */
     double lam;         /* proximal-gradient step (0.1)                         */
 } adp_en1d_params;

@@ -9,16 +9,15 @@
 // grad g(x)_S on the support S of x by CG and is z = -((B x - y) q^T + (B q) x^T);
 // Algorithm 2 (MAID) runs on top with the 2D problem's line search.
 //
-// Layout: a cluster of P CTAs.  CTA k holds rows k*m .. k*m+m-1 of B (m = n/P)
-// and the same columns, transposed (pitch n+1 against bank conflicts), in
-// shared memory, plus full copies of the vectors it needs.  A matrix-vector
-// product runs in two stages: B v by rows (each CTA its m entries, broadcast
-// into every CTA's copy through distributed shared memory), then B^T r by
-// columns.  A cluster barrier separates the stages; every reduction is summed
-// per CTA, its P partials broadcast and summed in the same order everywhere, so
-// every CTA takes every branch identically.  The trial operators of the line
-// search are never stored: B - alpha z = B + alpha (u q^T + w x^T) is formed
-// while the slices load from the current B.
+// Layout: a cluster of P CTAs.  For each operator the solves use (B, or a
+// trial of the line search), CTA k forms rows k*m .. k*m+m-1 (m = n/P) of the
+// Gram matrix M = B^T B and of c = B^T y in shared memory, so a lower-level
+// iteration is one product: grad f(x) = M x - c on this CTA's entries, x+ into
+// every CTA's copy of x through distributed shared memory, one cluster barrier.
+// Every reduction is summed per CTA, its P partials broadcast and summed in the
+// same order everywhere, so every CTA takes every branch identically.  The
+// trial operators are never stored: B - alpha z = B + alpha (u q^T + w x^T) is
+// formed while tiles of the current B stream through shared memory for M.
 #include "adp.h"
 
 #include <cooperative_groups.h>
@@ -41,6 +40,8 @@ constexpr int P = 8;        // CTAs per cluster
 constexpr int NT = 256;     // threads per CTA
 constexpr int NW = NT / 32;
 constexpr int NPART = 4;    // rotating partial-sum buffers
+constexpr int TB = 16;      // rows of B per tile while M forms
+constexpr int RB = 2;       // 4 x 4 output blocks of M per thread and pass
 
 enum Mode : int { M_LOWER = 0, M_UPPER, M_HYPER, M_MAID };
 
@@ -63,7 +64,7 @@ struct Job {
 size_t smem_bytes(int n)
 {
     const int m = n / P;
-    const size_t fl = (size_t)m * n + (size_t)m * (n + 1) + 9 * (size_t)n + 4 * (size_t)m;
+    const size_t fl = (size_t)m * n + (size_t)TB * n + 9 * (size_t)n + 5 * (size_t)m;
     return ((fl * 4 + 15) / 16) * 16 + (size_t)(NPART * P + NW) * 8;
 }
 
@@ -80,7 +81,7 @@ struct En {
     double a1, a2, lam, ilam;
     float thr, shrink, flam;   // prox constants: lam a1, 1 / (1 + 2 lam a2), lam
     const float *A, *AT, *y;
-    float *Brow, *BT, *x, *xn, *rv, *u, *w, *qf, *pf, *xb, *tC, *gC, *rC, *hC, *yR;
+    float *Mrow, *tile, *x, *xn, *rv, *u, *w, *qf, *pf, *xb, *tC, *gC, *rC, *hC, *yR, *cC;
     double *part, *red;
 
     __device__ En(const Job &jb, unsigned char *smem) : cl(cg::this_cluster())
@@ -103,8 +104,8 @@ struct En {
         AT = jb.AT;
         y = jb.y;
         float *f = reinterpret_cast<float *>(smem);
-        Brow = f; f += (size_t)m * n;
-        BT = f; f += (size_t)m * (n + 1);
+        Mrow = f; f += (size_t)m * n;
+        tile = f; f += (size_t)TB * n;
         x = f; f += n;
         xn = f; f += n;
         rv = f; f += n;
@@ -118,6 +119,7 @@ struct En {
         rC = f; f += m;
         hC = f; f += m;
         yR = f; f += m;                               // this CTA's entries of y
+        cC = f; f += m;                               // ... and of c = B^T y
         for (int i = threadIdx.x; i < m; i += blockDim.x) yR[i] = y[r0 + i];
         size_t off = (size_t)(reinterpret_cast<unsigned char *>(f) - smem);
         off = (off + 15) / 16 * 16;
@@ -171,24 +173,82 @@ struct En {
         return warp_sum_f(s);
     }
 
-    // this CTA's slices of the operator: B itself, or the trial
-    // B + al (uu q^T + ww xx^T) of the line search
-    __device__ void load_B(const float *B, float al, const float *uu, const float *q, const float *ww,
+    // this CTA's rows of M = Bt^T Bt and of c = Bt^T y for the operator
+    // Bt = B (al = 0) or the trial Bt = B + al (uu qq^T + ww xx^T) of the line
+    // search: tiles of TB rows of Bt through shared memory, each thread
+    // accumulating 4 x 4 blocks of M (rows in its warp's block, consecutive
+    // columns across lanes), the sums over the rows of B in order
+    __device__ void form_M(const float *B, float al, const float *uu, const float *qq, const float *ww,
                            const float *xx)
     {
-        for (int e = threadIdx.x; e < m * n; e += NT) {
-            const int il = e / n, j = e - il * n, i = r0 + il;
-            float v = B[(size_t)i * n + j];
-            if (al != 0.f) v = fmaf(al, fmaf(uu[i], q[j], ww[i] * xx[j]), v);
-            Brow[(size_t)il * n + j] = v;
-        }
-        for (int e = threadIdx.x; e < m * n; e += NT) {
-            const int i = e / m, jl = e - i * m, j = r0 + jl;
-            float v = B[(size_t)i * n + j];
-            if (al != 0.f) v = fmaf(al, fmaf(uu[i], q[j], ww[i] * xx[j]), v);
-            BT[(size_t)jl * (n + 1) + i] = v;
+        const int nk = n >> 2, nblk = (m >> 2) * nk;
+        for (int b0 = 0; b0 < nblk; b0 += NT * RB) {
+            float acc[RB][16];
+            int jb[RB], kb[RB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                const int bb = b0 + threadIdx.x + r * NT;
+                jb[r] = bb < nblk ? bb / nk : -1;
+                kb[r] = bb < nblk ? bb - (bb / nk) * nk : 0;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) acc[r][q] = 0.f;
+            }
+            float cacc = 0.f;
+            const bool cthr = b0 == 0 && threadIdx.x < m;
+            for (int i0 = 0; i0 < n; i0 += TB) {
+                const int rows = n - i0 < TB ? n - i0 : TB;
+                __syncthreads();                      // the previous tile is consumed
+                for (int e = threadIdx.x; e < rows * n; e += NT) {
+                    const int ii = e / n, j = e - ii * n, i = i0 + ii;
+                    float v = B[(size_t)i * n + j];
+                    if (al != 0.f) v = fmaf(al, fmaf(uu[i], qq[j], ww[i] * xx[j]), v);
+                    tile[e] = v;
+                }
+                __syncthreads();
+                for (int ii = 0; ii < rows; ++ii) {
+                    const float *tr = tile + (size_t)ii * n;
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) {
+                        if (jb[r] < 0) continue;
+                        const float4 av = *reinterpret_cast<const float4 *>(tr + r0 + 4 * jb[r]);
+                        const float4 bv = *reinterpret_cast<const float4 *>(tr + 4 * kb[r]);
+                        const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+                        for (int p = 0; p < 4; ++p)
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) acc[r][4 * p + q] = fmaf(a4[p], b4[q], acc[r][4 * p + q]);
+                    }
+                    if (cthr) cacc = fmaf(tr[r0 + threadIdx.x], yfull(i0 + ii), cacc);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                if (jb[r] < 0) continue;
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+                    *reinterpret_cast<float4 *>(Mrow + (size_t)(4 * jb[r] + p) * n + 4 * kb[r]) =
+                        make_float4(acc[r][4 * p], acc[r][4 * p + 1], acc[r][4 * p + 2], acc[r][4 * p + 3]);
+            }
+            if (cthr) cC[threadIdx.x] = cacc;
         }
         __syncthreads();
+    }
+    __device__ float yfull(int i) const { return __ldg(y + i); }
+
+    // rows r0 .. r0+m-1 of Bt (= B + al (uu qq^T + ww xx^T)) times v, from global
+    // memory: the total of row il in lane 0
+    __device__ float brow_dot(const float *B, float al, const float *uu, const float *qq, const float *ww,
+                              const float *xx, int il, const float *v) const
+    {
+        const int i = r0 + il;
+        const float *row = B + (size_t)i * n;
+        float s = 0.f;
+        for (int j = lane; j < n; j += 32) {
+            float bv = __ldg(row + j);
+            if (al != 0.f) bv = fmaf(al, fmaf(uu[i], qq[j], ww[i] * xx[j]), bv);
+            s = fmaf(bv, v[j], s);
+        }
+        return warp_sum_f(s);
     }
 
     __device__ float prox(float v) const
@@ -203,16 +263,11 @@ struct En {
     {
         int it = 0;
         for (;;) {
-            // r = B x - y, by rows
-            for (int il = warp; il < m; il += NW) {
-                const float s = row_dot(Brow, n, il, x);
-                put_all(rv, r0 + il, s - yR[il]);
-            }
-            csync();
-            // x+ = prox(x - lam B^T r), by columns; G = (x - x+) / lam
+            // x+ = prox(x - lam (M x - c)) on this CTA's entries, into every CTA;
+            // G = (x - x+) / lam
             double gl = 0.0;
             for (int jl = warp; jl < m; jl += NW) {
-                const float s = row_dot(BT, n + 1, jl, rv);
+                const float s = row_dot(Mrow, n, jl, x) - cC[jl];
                 const float xc = x[r0 + jl];
                 const float xp = prox(xc - flam * s);
                 put_all(xn, r0 + jl, xp);
@@ -260,9 +315,10 @@ struct En {
     }
 
     // Algorithm 1, steps 2-3, at the member x (its gradient slice in gC from
-    // upper): CG on the support; q in qf, u = B x - y in u, w = B q in w (all
-    // full); returns iterations; zz = ||z||^2
-    __device__ int hyper(double delta, int max_iters, double &res, double &zz)
+    // upper, M of the operator B in Mrow): CG on the support; q in qf,
+    // u = B x - y in u, w = B q in w (all full, B's rows read from global
+    // memory); returns iterations; zz = ||z||^2
+    __device__ int hyper(const float *B, double delta, int max_iters, double &res, double &zz)
     {
         double rl = 0.0;
         for (int jl = threadIdx.x; jl < m; jl += NT) {
@@ -279,14 +335,9 @@ struct En {
         double rr = cluster_sum(rl);
         int it = 0;
         while (sqrt(rr) > delta && it < max_iters) {
-            for (int il = warp; il < m; il += NW) {   // w = B p by rows
-                const float s = row_dot(Brow, n, il, pf);
-                put_all(w, r0 + il, s);
-            }
-            csync();
             double pl = 0.0;
-            for (int jl = warp; jl < m; jl += NW) {   // H p on this CTA's columns
-                const float s = row_dot(BT, n + 1, jl, w);
+            for (int jl = warp; jl < m; jl += NW) {   // H p = M p + 2 a2 p on this CTA's entries of S
+                const float s = row_dot(Mrow, n, jl, pf);
                 if (lane == 0) {
                     const float pc = pf[r0 + jl];
                     const float hp = x[r0 + jl] != 0.f ? fmaf((float)(2.0 * a2), pc, s) : 0.f;
@@ -324,8 +375,8 @@ struct En {
         }
         csync();
         for (int il = warp; il < m; il += NW) {
-            const float s1 = row_dot(Brow, n, il, x);
-            const float s2 = row_dot(Brow, n, il, qf);
+            const float s1 = brow_dot(B, 0.f, nullptr, nullptr, nullptr, nullptr, il, x);
+            const float s2 = brow_dot(B, 0.f, nullptr, nullptr, nullptr, nullptr, il, qf);
             put_all(u, r0 + il, s1 - yR[il]);
             put_all(w, r0 + il, s2);
         }
@@ -357,7 +408,7 @@ __device__ bool maid_step(En &e, const Job &jb, adp_maid_state &s)
         s.stopped = 1;
         return false;
     }
-    e.load_B(jb.B, 0.f, nullptr, nullptr, nullptr, nullptr);
+    e.form_M(jb.B, 0.f, nullptr, nullptr, nullptr, nullptr);
     for (int i = threadIdx.x; i < e.n; i += NT) e.x[i] = jb.x[i];
     __syncthreads();
     int j = s.max_bt;
@@ -369,15 +420,14 @@ __device__ bool maid_step(En &e, const Job &jb, adp_maid_state &s)
         double l0, gx0;
         e.upper(e.x, l0, gx0);
         double res, zz;
-        const int cit = e.hyper(s.delta, s.cg_max_iters, res, zz);
+        const int cit = e.hyper(jb.B, s.delta, s.cg_max_iters, res, zz);
         s.cg_iters += cit;
         if (res > s.delta) s.cg_capped = 1;
         s.znorm = sqrt(zz);
         e.copy_vec(e.xb, e.x);                        // x~(b_k): the trials' warm start
         for (int i = 0; i < j; ++i) {
             s.trials += 1;
-            e.csync();                                // the slices are read by every CTA's products
-            e.load_B(jb.B, (float)s.step, e.u, e.qf, e.w, e.xb);
+            e.form_M(jb.B, (float)s.step, e.u, e.qf, e.w, e.xb);
             e.copy_vec(e.x, e.xb);
             e.csync();
             s.ll_iters += e.lower(s.eps, s.ll_max_iters, gn);
@@ -389,10 +439,12 @@ __device__ bool maid_step(En &e, const Job &jb, adp_maid_state &s)
             s.psi = psi;
             if (psi <= 0.0) {
                 // b_{k+1}: this CTA's rows of the trial operator, and x~(b_{k+1})
-                e.csync();
+                e.csync();                            // every CTA has formed its M from B
+                const float al = (float)s.step;
                 for (int q = threadIdx.x; q < e.m * e.n; q += NT) {
-                    const int il = q / e.n, jj = q - il * e.n;
-                    jb.B[(size_t)(e.r0 + il) * e.n + jj] = e.Brow[q];
+                    const int il = q / e.n, jj = q - il * e.n, i = e.r0 + il;
+                    float *bp = jb.B + (size_t)i * e.n + jj;
+                    *bp = fmaf(al, fmaf(e.u[i], e.qf[jj], e.w[i] * e.xb[jj]), *bp);
                 }
                 if (e.k == 0)
                     for (int q = threadIdx.x; q < e.n; q += NT) jb.x[q] = e.x[q];
@@ -414,7 +466,7 @@ __device__ bool maid_step(En &e, const Job &jb, adp_maid_state &s)
         s.delta *= s.nu_down;
         // the next round starts again from b_k and x~(b_k)
         e.csync();
-        e.load_B(jb.B, 0.f, nullptr, nullptr, nullptr, nullptr);
+        e.form_M(jb.B, 0.f, nullptr, nullptr, nullptr, nullptr);
         e.copy_vec(e.x, e.xb);
         e.csync();
         if (s.eps_stop > 0.0 && s.eps <= s.eps_stop) {
@@ -432,7 +484,7 @@ __global__ void __launch_bounds__(NT, 1) en1d_kernel(const __grid_constant__ Job
     const bool lead = e.k == 0 && threadIdx.x == 0;
     switch (jb.mode) {
     case M_LOWER: {
-        e.load_B(jb.B, 0.f, nullptr, nullptr, nullptr, nullptr);
+        e.form_M(jb.B, 0.f, nullptr, nullptr, nullptr, nullptr);
         for (int i = threadIdx.x; i < e.n; i += NT) e.x[i] = jb.x[i];
         e.csync();
         double gn;
@@ -457,12 +509,12 @@ __global__ void __launch_bounds__(NT, 1) en1d_kernel(const __grid_constant__ Job
         break;
     }
     case M_HYPER: {
-        e.load_B(jb.B, 0.f, nullptr, nullptr, nullptr, nullptr);
+        e.form_M(jb.B, 0.f, nullptr, nullptr, nullptr, nullptr);
         for (int i = threadIdx.x; i < e.n; i += NT) e.x[i] = jb.x[i];
         e.csync();
         double l, g, res, zz;
         e.upper(e.x, l, g);
-        const int it = e.hyper(jb.delta, jb.max_iters, res, zz);
+        const int it = e.hyper(jb.B, jb.delta, jb.max_iters, res, zz);
         for (int q = threadIdx.x; q < e.m * e.n; q += NT) {
             const int il = q / e.n, j = q - il * e.n, i = e.r0 + il;
             jb.z[(size_t)i * e.n + j] = -fmaf(e.u[i], e.qf[j], e.w[i] * e.x[j]);
@@ -569,8 +621,8 @@ adp_status adp_en1d_create(const adp_en1d_params *prm, const float *A, const flo
         return ADP_EINVAL;
     }
     *out = nullptr;
-    if (prm->n < P || prm->n > ADP_EN1D_MAX_N || prm->n % P) {
-        err("n must be a multiple of 8 in 8 .. %s%lld", "", ADP_EN1D_MAX_N);
+    if (prm->n < 4 * P || prm->n > ADP_EN1D_MAX_N || prm->n % (4 * P)) {
+        err("n must be a multiple of 32 in 32 .. %s%lld", "", ADP_EN1D_MAX_N);
         return ADP_EINVAL;
     }
     if (!(prm->a1 >= 0.0) || !(prm->a2 >= 0.0) || !(prm->lam > 0.0)) {

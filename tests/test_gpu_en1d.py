@@ -3,8 +3,9 @@ csrc/adp_en1d.cu) against the FP64 oracle (oracle/en1d.py), through the C ABI.
 
 Both sides see the same FP32-representable inputs.  The GPU computes in FP32
 with FP64 dot products, norms and line-search tests, so:
-* iteration-matched proximal-gradient iterates and the gradient-mapping norm
-  agree to 1e-5 relative, eps-stopped solves stop within one iteration;
+* iteration-matched proximal-gradient iterates agree to 1e-5 relative and the
+  gradient-mapping norm to 1e-5 relative plus 2e-6 (the Gram form's absolute
+  rounding), eps-stopped solves stop within one iteration;
 * the upper loss and its gradient norm agree to 1e-6;
 * iteration-matched support CG (q) and the hypergradient z agree to 1e-4, and
   so does z from CG run to tolerance;
@@ -63,7 +64,9 @@ def test_lower_solve_iteration_matched(n, perturb):
         xo, ito, gno = pr.P.lower_solve(pr.B, pr.y, 0.0, k)
         assert it == ito == k
         assert rel(pr.h(xg), xo) <= 1e-5
-        assert abs(gn - gno) <= 1e-5 * gno
+        # the GPU forms grad f as (B^T B) x - B^T y: its rounding is absolute,
+        # ~u ||B^T B|| ||x|| (about 5e-7 here), whatever the size of G
+        assert abs(gn - gno) <= 1e-5 * gno + 2e-6
 
 
 @pytest.mark.parametrize("eps", [1e-2, 1e-3])
