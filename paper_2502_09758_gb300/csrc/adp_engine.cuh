@@ -187,31 +187,25 @@ struct Eng {
         if (ox && oy) B[o + ox + oy] = v;
     }
 
-    // Every ghost copy of rows i0 .. i0+nr-1 of channel c of B: each padded
-    // position (ii, jj) with ii = i (mod H) and jj = j (mod W), other than
-    // the pixel (i, j) itself, gets val(i - i0, j).  The same positions as
-    // put() writes for every pixel of those rows (all threads take part).
+    // The ghost rows that the real-to-complex phases read, for rows i0 ..
+    // i0+nr-1 of channel c of B: image row 0 into padded row H and image row
+    // H-1 into padded row -1, interior columns only (val(i - i0, j) gives
+    // pixel (i, j)).  Those phases stage rows with one halo row on each side
+    // and wrap their stencils' columns in shared memory, so no other ghost
+    // cell of the buffers they write is ever read (their CG update keeps its
+    // ghost rows at distance 1 from these).
     template <typename V>
-    __device__ void ghost_rows(T *B, int c, int i0, int nr, V val) const
+    __device__ void halo_rows(T *B, int c, int i0, int nr, V val) const
     {
-        const int H = cx.H, W = cx.W, Gx = cx.Gx, Gy = cx.Gy, Wg = W + 2 * Gx;
-        T *base = B + c * cx.HWp;
-        auto col = [=](int jj) { const int js = jj % W; return js < 0 ? js + W : js; };
-        // the ghost columns of the rows themselves
-        for (int q = threadIdx.x; q < nr * 2 * Gx; q += blockDim.x) {
-            const int r = q / (2 * Gx), k = q - r * 2 * Gx, jj = k < Gx ? k - Gx : W + k - Gx;
-            base[(long long)(i0 + r + Gy) * cx.Wp + jj + Gx] = val(r, col(jj));
+        const int H = cx.H, W = cx.W;
+        T *base = B + c * cx.HWp + cx.Gx;
+        if (i0 == 0) {
+            T *row = base + (long long)(H + cx.Gy) * cx.Wp;
+            for (int j = threadIdx.x; j < W; j += blockDim.x) row[j] = val(0, j);
         }
-        // whole ghost rows: row i has copies at i + m H (m != 0) only when
-        // i < Gy or i >= H - Gy
-        for (int r = 0; r < nr; ++r) {
-            const int i = i0 + r;
-            if (i >= Gy && i < H - Gy) continue;
-            for (int ii = i - ((i + Gy) / H) * H; ii < H + Gy; ii += H) {
-                if (ii == i) continue;
-                T *row = base + (long long)(ii + Gy) * cx.Wp;   // image column -Gx at row[0]
-                for (int q = threadIdx.x; q < Wg; q += blockDim.x) row[q] = val(r, col(q - Gx));
-            }
+        if (i0 + nr == H) {
+            T *row = base + (long long)(cx.Gy - 1) * cx.Wp;
+            for (int j = threadIdx.x; j < W; j += blockDim.x) row[j] = val(nr - 1, j);
         }
     }
 
@@ -772,12 +766,12 @@ struct Eng {
     //   RF_FWD:   forward row DFTs of buffer b1 into fzh / fzn.
     //   RF_FISTA: G = B^T B y_k - B^T y_delta + alpha grad J(y_k), y_k in b1,
     //             x_k in b2, B^T y_delta in cx.fc; x_{k+1} = y_k - tau_c G into bo1, y_{k+1} =
-    //             x_{k+1} + sc (x_{k+1} - x_k) into bo2 (with its ghosts);
+    //             x_{k+1} + sc (x_{k+1} - x_k) into bo2 (with its halo rows);
     //             forward row DFTs of y_{k+1}; returns sum G^2.
     //   RF_CGP:   p = r + sc p_prev (r in b1, p_prev in b2; p = r when b2 < 0)
-    //             into bo1 (with its ghosts); forward row DFTs of p.
+    //             into bo1 (with its halo rows); forward row DFTs of p.
     //   RF_HESS:  Hp = B^T B p + alpha D^T(phi''(D x) . D p), p in b1 (with
-    //             ghosts), x in b2, into bo1 (with its ghosts); returns sum p Hp.
+    //             halo rows), x in b2, into bo1 (with its halo rows); returns sum p Hp.
     __device__ S rows_r2c(int mode, int b1, int b2, int bo1, int bo2, T sc)
     {
         S part = Sc::zero();
@@ -812,6 +806,7 @@ struct Eng {
             }
             for (int t = bid; t < ntask && !ffail; t += nblk, ++u) {
                 const int c = t / tpc, i0 = (t - c * tpc) * 2 * RP;
+                const bool edge = i0 == 0 || i0 + 2 * RP == H;   // the task writes halo rows
                 float *st = rstage(dbl ? (u & 1) : 0);
                 const bool nxt = dbl && t + nblk < ntask;
                 if (!dbl) {
@@ -918,14 +913,14 @@ struct Eng {
                     else pixels(std::integral_constant<int, 2>());
                     fence_proxy_async_smem();  // the row buffer's reads, before its refill
                     __syncthreads();
-                    ghost_rows(O2, c, i0, 2 * RP, [&](int r, int j) {
+                    halo_rows(O2, c, i0, 2 * RP, [&](int r, int j) {
                         const float2 z = wa[slot(r >> 1, j)];
                         return (r & 1) ? z.y : z.x;
                     });
                     // the row buffer is free: the next task's rows load under
                     // the forward passes
                     if (nxt) rtask_rows(t + nblk, mode, b1, b2);
-                    __syncthreads();               // the ghost copies have read the work area
+                    if (edge) __syncthreads();     // the halo rows have read the work area
                     fft_pass_n<0>(lpass(np - 1), W, RP, lrp, cx.ftwW, spass(np - 1), ld_wa, nomid, st_wa);
                     __syncthreads();
                 } else if (mode == RF_HESS) {
@@ -993,15 +988,14 @@ struct Eng {
                     fence_proxy_async_smem();  // the row buffer's reads, before its refill
                     __syncthreads();
                     if (nxt) rtask_rows(t + nblk, mode, b1, b2);   // the row buffer is free
-                    ghost_rows(O1, c, i0, 2 * RP, [&](int r, int j) {
+                    halo_rows(O1, c, i0, 2 * RP, [&](int r, int j) {
                         const float2 z = wa[slot(r >> 1, j)];
                         return (r & 1) ? z.y : z.x;
                     });
-                    __syncthreads();           // the work area is rewritten by the next task
-                    continue;                  // no forward transform
+                    continue;                  // no forward transform (the next task starts with a barrier)
                 } else {
                     // RF_FWD / RF_CGP: the staged image rows (RF_CGP: p = r + sc
-                    // p_prev, to global memory with its ghost copies) into the
+                    // p_prev, to global memory with its halo rows) into the
                     // work area in natural order, four consecutive pixels of
                     // both rows of a pair per thread
                     if (!rows_landed()) break;
@@ -1030,11 +1024,11 @@ struct Eng {
                     __syncthreads();
                     if (nxt) rtask_rows(t + nblk, mode, b1, b2);   // under the forward passes
                     if (mode == RF_CGP) {
-                        ghost_rows(O1, c, i0, 2 * RP, [&](int r, int j) {
+                        halo_rows(O1, c, i0, 2 * RP, [&](int r, int j) {
                             const float2 z = wa[slot(r >> 1, j)];
                             return (r & 1) ? z.y : z.x;
                         });
-                        __syncthreads();       // the ghost copies have read the work area
+                        if (edge) __syncthreads();   // the halo rows have read the work area
                     }
                     fft_pass_n<0>(lpass(np - 1), W, RP, lrp, cx.ftwW, spass(np - 1), ld_wa, nomid, st_wa);
                     __syncthreads();
