@@ -13,7 +13,7 @@ from the paper's definitions in its order:
   (Sec. 4.1: "proximal-gradient descent method with step size lambda_x");
 * Algorithm 1 (InexactGradient) and Algorithm 2 (MAID) as for the 2D problem.
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent:
 * the 1/2 on the data term of h, as in the 2D readings;
 * the accuracy of a lower-level iterate is the norm of the proximal-gradient
   mapping G(x) = (x - prox(x - lam grad f(x))) / lam, which equals grad h
