@@ -644,7 +644,10 @@ adp_status adp_en1d_create(const adp_en1d_params *prm, const float *A, const flo
         adp_en1d_destroy(p);
         return st;
     };
-    if (cudaGetDevice(&p->device) != cudaSuccess) return fail(ADP_ECUDA);
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        err("no current CUDA device%s", "", 0);
+        return fail(ADP_ECUDA);
+    }
     {
         int maxsmem = 0;
         cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
