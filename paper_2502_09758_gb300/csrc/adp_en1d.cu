@@ -23,7 +23,6 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
-#include <mutex>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
