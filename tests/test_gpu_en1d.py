@@ -174,7 +174,7 @@ def test_invalid_sizes_are_rejected():
     y = torch.zeros(100, device="cuda")
     A = torch.zeros((100, 100), device="cuda")
     with pytest.raises(adp.AdpError):
-        adp.En1d(A, y)                       # not a multiple of 8
+        adp.En1d(A, y)                       # not a multiple of 32
     y = torch.zeros(392, device="cuda")
     A = torch.zeros((392, 392), device="cuda")
     with pytest.raises(adp.AdpError):
