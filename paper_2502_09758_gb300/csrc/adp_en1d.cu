@@ -23,6 +23,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -547,10 +548,13 @@ __global__ void __launch_bounds__(NT, 1) en1d_kernel(const __grid_constant__ Job
     e.csync();                                        // no CTA leaves while others read its shared memory
 }
 
-void err(const char *fmt, const char *a = "", long long v = 0)
+__attribute__((format(printf, 1, 2))) void err(const char *fmt, ...)
 {
     char b[512];
-    snprintf(b, sizeof b, fmt, a, v);
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b, sizeof b, fmt, ap);
+    va_end(ap);
     adp::record_error(b);
 }
 
@@ -616,21 +620,21 @@ extern "C" {
 adp_status adp_en1d_create(const adp_en1d_params *prm, const float *A, const float *y, void *stream, adp_en1d **out)
 {
     if (!prm || !A || !y || !out) {
-        err("null argument%s", "", 0);
+        err("null argument");
         return ADP_EINVAL;
     }
     *out = nullptr;
     if (prm->n < 4 * P || prm->n > ADP_EN1D_MAX_N || prm->n % (4 * P)) {
-        err("n must be a multiple of 32 in 32 .. %s%lld", "", ADP_EN1D_MAX_N);
+        err("n must be a multiple of 32 in 32 .. %d", ADP_EN1D_MAX_N);
         return ADP_EINVAL;
     }
     if (!(prm->a1 >= 0.0) || !(prm->a2 >= 0.0) || !(prm->lam > 0.0)) {
-        err("a1, a2 must be >= 0 and lam > 0%s", "", 0);
+        err("a1, a2 must be >= 0 and lam > 0");
         return ADP_EINVAL;
     }
     adp_en1d *p = (adp_en1d *)calloc(1, sizeof(adp_en1d));
     if (!p) {
-        err("host allocation failed%s", "", 0);
+        err("host allocation failed");
         return ADP_ENOMEM;
     }
     p->prm = *prm;
@@ -644,14 +648,14 @@ adp_status adp_en1d_create(const adp_en1d_params *prm, const float *A, const flo
         return st;
     };
     if (cudaGetDevice(&p->device) != cudaSuccess) {
-        err("no current CUDA device%s", "", 0);
+        err("no current CUDA device");
         return fail(ADP_ECUDA);
     }
     {
         int maxsmem = 0;
         cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
         if ((size_t)maxsmem < p->smem) {
-            err("shared memory per CTA too small for n%s = %lld", "", n);
+            err("shared memory per CTA too small for n = %d", n);
             return fail(ADP_EINVAL);
         }
         cudaError_t e = cudaFuncSetAttribute(en1d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
@@ -665,7 +669,7 @@ adp_status adp_en1d_create(const adp_en1d_params *prm, const float *A, const flo
         cudaMalloc((void **)&p->st_d, sizeof(adp_maid_state)) != cudaSuccess ||
         cudaMallocHost((void **)&p->out_h, sizeof(Out)) != cudaSuccess ||
         cudaMallocHost((void **)&p->st_h, sizeof(adp_maid_state)) != cudaSuccess) {
-        err("device allocation failed%s", "", 0);
+        err("device allocation failed");
         return fail(ADP_ENOMEM);
     }
     // A^T and the bound 2 ||A||_1 ||A||_inf, from a host copy of A
@@ -673,7 +677,7 @@ adp_status adp_en1d_create(const adp_en1d_params *prm, const float *A, const flo
     if (!h || !ht) {
         free(h);
         free(ht);
-        err("host allocation failed%s", "", 0);
+        err("host allocation failed");
         return fail(ADP_ENOMEM);
     }
     cudaError_t e = cudaMemcpyAsync(h, A, (size_t)n * n * sizeof(float), cudaMemcpyDeviceToHost, p->stream);
@@ -718,7 +722,7 @@ adp_status adp_en1d_create(const adp_en1d_params *prm, const float *A, const flo
         cfg.attrs = at;
         cfg.numAttrs = 1;
         if (cudaOccupancyMaxActiveClusters(&ncl, en1d_kernel, &cfg) != cudaSuccess || ncl < 1) {
-            err("a cluster of 8 CTAs with this shared memory cannot be resident%s", "", 0);
+            err("a cluster of 8 CTAs with this shared memory cannot be resident");
             return fail(ADP_EINVAL);
         }
     }
@@ -743,7 +747,7 @@ adp_status adp_en1d_lower_solve(adp_en1d *p, const float *B, float *x, double ep
                                 double *gmap_norm)
 {
     if (!p || !B || !x || max_iters < 0) {
-        err("invalid arguments%s", "", 0);
+        err("invalid arguments");
         return ADP_EINVAL;
     }
     Job jb = {};
@@ -762,7 +766,7 @@ adp_status adp_en1d_lower_solve(adp_en1d *p, const float *B, float *x, double ep
 adp_status adp_en1d_upper_loss(adp_en1d *p, const float *x, double *loss, double *gradx_norm)
 {
     if (!p || !x) {
-        err("invalid arguments%s", "", 0);
+        err("invalid arguments");
         return ADP_EINVAL;
     }
     Job jb = {};
@@ -779,7 +783,7 @@ adp_status adp_en1d_hypergrad(adp_en1d *p, const float *B, const float *x, doubl
                               float *z, int *cg_iters, double *resnorm)
 {
     if (!p || !B || !x || !q || !z || max_iters < 0) {
-        err("invalid arguments%s", "", 0);
+        err("invalid arguments");
         return ADP_EINVAL;
     }
     Job jb = {};
@@ -800,7 +804,7 @@ adp_status adp_en1d_hypergrad(adp_en1d *p, const float *B, const float *x, doubl
 adp_status adp_en1d_maid_init(adp_en1d *p, adp_maid_state *s)
 {
     if (!p || !s) {
-        err("invalid arguments%s", "", 0);
+        err("invalid arguments");
         return ADP_EINVAL;
     }
     memset(s, 0, sizeof *s);
@@ -824,7 +828,7 @@ adp_status adp_en1d_maid_init(adp_en1d *p, adp_maid_state *s)
 static adp_status maid_launch(adp_en1d *p, adp_maid_state *s, float *B, float *x, int max_steps, int *steps)
 {
     if (!p || !s || !B || !x || max_steps < 1) {
-        err("invalid arguments%s", "", 0);
+        err("invalid arguments");
         return ADP_EINVAL;
     }
     *p->st_h = *s;
